@@ -1,0 +1,269 @@
+"""Seeded synthetic inputs: atomic structures, parameter sets, frequency grids.
+
+This module holds no arithmetic of the omega-FQ method itself -- only positions
+(bohr), parameter values (atomic units) and frequency lists.  It is the one
+module that both the CUDA path and the CPU oracle take their inputs from.
+
+Structures follow the systems of the paper's Section 4: chiral and armchair
+carbon nanotubes (Table "CNT data"), graphene disks cut from the honeycomb
+lattice (Table "GD data"), hexagonal graphene flakes, and fcc metal
+nanoparticles (the sodium nanorod system of Section 4.4 is 3D fcc metal).
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+BOHR_PER_ANGSTROM = 1.0 / 0.529177210903
+HARTREE_EV = 27.211386245988
+C_AU = 137.035999084          # speed of light, atomic units
+
+CC_BOND_ANG = 1.42            # graphene C-C distance (Section 4, CNT/GD structures)
+GRAPHENE_A_ANG = CC_BOND_ANG * math.sqrt(3.0)   # lattice constant, 2.4595 A
+
+
+def ev(x):
+    """Energy in eV -> hartree (frequencies are given to the library in hartree)."""
+    return np.asarray(x, dtype=np.float64) / HARTREE_EV
+
+
+# --------------------------------------------------------------------------- params
+# Parameter values are not printed in the paper (they are taken there from earlier
+# works); these are this project's documented, unpinned choices.  Only the
+# combination 2 n0 * area enters the solution, and the GPU path and the oracle
+# always receive the same values.
+
+def carbon_params(eps_fermi_ev: float = 1.51, tau: float = 170.0) -> dict:
+    """Graphene / nanotube parameter set (atomic units).
+
+    r0: C-C equilibrium distance; widths from eta via the Eq. 4 width rule; the
+    Drude density scales linearly with the Fermi energy (higher eps_F -> more
+    carriers, blue shift, as described in Section 4.1)."""
+    return {
+        "eta": 0.60,
+        "d_fermi": 12.0,
+        "s_fermi": 1.1,
+        "r0": CC_BOND_ANG * BOHR_PER_ANGSTROM,
+        "area": 1.0,
+        "n0": 0.010 * (eps_fermi_ev / 1.51),
+        "tau": float(tau),
+        "cutoff_eps": 1e-16,
+    }
+
+
+def sodium_params(tau: float = 170.0) -> dict:
+    """fcc sodium-like metal parameter set (atomic units); r0 = a/sqrt(2) for a = 4.23 A."""
+    return {
+        "eta": 0.35,
+        "d_fermi": 12.0,
+        "s_fermi": 1.1,
+        "r0": 4.23 / math.sqrt(2.0) * BOHR_PER_ANGSTROM,
+        "area": 1.0,
+        "n0": 0.0080,
+        "tau": float(tau),
+        "cutoff_eps": 1e-16,
+    }
+
+
+# --------------------------------------------------------------------------- graphene
+
+def _graphene_vectors():
+    a = GRAPHENE_A_ANG
+    a1 = np.array([a, 0.0])
+    a2 = np.array([0.5 * a, 0.5 * math.sqrt(3.0) * a])
+    return a1, a2
+
+
+def honeycomb_flake(n_rings: int) -> np.ndarray:
+    """Hexagonal graphene flake with zigzag edges, n_rings hexagons per edge:
+    6 n^2 atoms (benzene n=1, coronene n=2, ...).  Planar (z = 0), centred, bohr."""
+    if n_rings < 1:
+        raise ValueError("n_rings >= 1")
+    a1, a2 = _graphene_vectors()
+    delta = (a1 + a2) / 3.0
+    pts = {}
+    for i in range(-(n_rings - 1), n_rings):
+        for j in range(-(n_rings - 1), n_rings):
+            if max(abs(i), abs(j), abs(i + j)) > n_rings - 1:
+                continue
+            c = i * a1 + j * a2 + 2.0 * delta
+            for k in range(6):
+                th = math.radians(90.0 + 60.0 * k)
+                p = c + CC_BOND_ANG * np.array([math.cos(th), math.sin(th)])
+                key = (round(p[0] * 1e5), round(p[1] * 1e5))
+                pts[key] = p
+    xy = np.array([pts[k] for k in sorted(pts)])
+    xy -= xy.mean(axis=0)
+    xyz = np.zeros((len(xy), 3))
+    xyz[:, :2] = xy
+    return xyz * BOHR_PER_ANGSTROM
+
+
+def graphene_disk(diameter_nm: float, vacancy_frac: float = 0.0, seed: int | None = None):
+    """Graphene disk cut from the honeycomb lattice around a hexagon centre,
+    all atoms with |r| < d/2 kept (dangling atoms on the edge are retained, as
+    in Section 4.2).  Optionally a fraction of atoms is removed as vacancies by
+    a seeded uniform draw.  Planar (z = 0), bohr."""
+    a1, a2 = _graphene_vectors()
+    delta = (a1 + a2) / 3.0
+    centre = 2.0 * delta
+    R = 0.5 * diameter_nm * 10.0
+    m = int(math.ceil(R / GRAPHENE_A_ANG * 1.2)) + 3
+    i, j = np.meshgrid(np.arange(-m, m + 1), np.arange(-m, m + 1), indexing="ij")
+    i = i.ravel().astype(np.float64)
+    j = j.ravel().astype(np.float64)
+    A = np.outer(i, a1) + np.outer(j, a2)
+    B = A + delta
+    P = np.concatenate([A, B]) - centre
+    keep = np.einsum("ij,ij->i", P, P) < R * R
+    P = P[keep]
+    order = np.lexsort((P[:, 0], P[:, 1]))
+    P = P[order]
+    if vacancy_frac > 0.0:
+        rng = np.random.default_rng(seed)
+        nrem = int(round(vacancy_frac * len(P)))
+        drop = rng.choice(len(P), size=nrem, replace=False)
+        mask = np.ones(len(P), dtype=bool)
+        mask[drop] = False
+        P = P[mask]
+    xyz = np.zeros((len(P), 3))
+    xyz[:, :2] = P
+    return xyz * BOHR_PER_ANGSTROM
+
+
+def nanotube_cell(n: int, m: int):
+    """Translational unit cell of the (n, m) nanotube: returns
+    (atoms_per_cell, period_angstrom, diameter_angstrom)."""
+    dR = math.gcd(2 * m + n, 2 * n + m)
+    nhex = 2 * (n * n + m * m + n * m) // dR
+    ch = GRAPHENE_A_ANG * math.sqrt(n * n + m * m + n * m)
+    period = math.sqrt(3.0) * ch / dR
+    return 2 * nhex, period, ch / math.pi
+
+
+def nanotube(n: int, m: int, ncells: int) -> np.ndarray:
+    """(n, m) single-walled carbon nanotube of `ncells` translational unit cells,
+    rolled from the honeycomb lattice; axis along z, centred, bohr.  The atom
+    count is exactly ncells * atoms_per_cell (e.g. (8,12) x 27 cells = 8208)."""
+    if n < 0 or m < 0 or n + m == 0:
+        raise ValueError("bad chirality")
+    dR = math.gcd(2 * m + n, 2 * n + m)
+    t1 = (2 * m + n) // dR
+    t2 = -(2 * n + m) // dR
+    den = n * t2 - m * t1              # lattice-units cross product C_h x T
+    # lattice points (u, v) -> alpha along C_h, beta along T, both exact rationals
+    corners_u = [0, n, ncells * t1, n + ncells * t1]
+    corners_v = [0, m, ncells * t2, m + ncells * t2]
+    ui = np.arange(min(corners_u) - 2, max(corners_u) + 3)
+    vi = np.arange(min(corners_v) - 2, max(corners_v) + 3)
+    U, V = np.meshgrid(ui, vi, indexing="ij")
+    U = U.ravel().astype(np.int64)
+    V = V.ravel().astype(np.int64)
+    out = []
+    for off in (0, 1):                 # sublattice A at (u, v), B at (u + 1/3, v + 1/3)
+        U3 = 3 * U + off
+        V3 = 3 * V + off
+        an = U3 * t2 - V3 * t1         # alpha = an / (3 den)
+        bn = n * V3 - m * U3           # beta  = bn / (3 den)
+        d3 = 3 * den
+        if d3 < 0:
+            an, bn, d3 = -an, -bn, -d3
+        ok = (an >= 0) & (an < d3) & (bn >= 0) & (bn < ncells * d3)
+        out.append(np.stack([an[ok] / d3, bn[ok] / d3], axis=1))
+    ab = np.concatenate(out)
+    cnt, period, diam = nanotube_cell(n, m)
+    assert len(ab) == cnt * ncells, (len(ab), cnt * ncells)
+    radius = 0.5 * diam
+    phi = 2.0 * math.pi * ab[:, 0]
+    zc = ab[:, 1] * period
+    xyz = np.stack([radius * np.cos(phi), radius * np.sin(phi), zc], axis=1)
+    xyz[:, 2] -= 0.5 * ncells * period
+    order = np.lexsort((phi, xyz[:, 2]))
+    return xyz[order] * BOHR_PER_ANGSTROM
+
+
+def fcc_sphere(a_ang: float, radius_ang: float, jitter_ang: float = 0.0,
+               seed: int | None = None) -> np.ndarray:
+    """Atom-centred fcc nanosphere (lattice constant a, all sites with |r| <= R).
+    Surface atoms -- fewer than 12 neighbours within 1.1 * a / sqrt(2) -- are
+    displaced by a seeded U(-jitter, +jitter) per coordinate.  Bohr."""
+    m = int(math.ceil(radius_ang / a_ang)) + 1
+    g = np.arange(-m, m + 1)
+    I, J, K = np.meshgrid(g, g, g, indexing="ij")
+    base = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1).astype(np.float64)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    P = (base[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a_ang
+    P = P[np.einsum("ij,ij->i", P, P) <= radius_ang ** 2 * (1 + 1e-12)]
+    P = P[np.lexsort((P[:, 0], P[:, 1], P[:, 2]))]
+    if jitter_ang > 0.0:
+        from scipy.spatial import cKDTree
+        tree = cKDTree(P)
+        nn = tree.query_ball_point(P, r=1.1 * a_ang / math.sqrt(2.0), return_length=True) - 1
+        surf = nn < 12
+        rng = np.random.default_rng(seed)
+        shift = rng.uniform(-jitter_ang, jitter_ang, size=(len(P), 3))
+        P = P + shift * surf[:, None]
+    return P * BOHR_PER_ANGSTROM
+
+
+def fcc_sphere_radius_for(n_atoms: int, a_ang: float) -> float:
+    """Sphere radius (A) whose volume holds about n_atoms fcc sites (4 per a^3)."""
+    return (3.0 * n_atoms * a_ang ** 3 / (4.0 * 4.0 * math.pi)) ** (1.0 / 3.0)
+
+
+def random_cluster(n: int, seed: int, spacing_bohr: float = 2.7, jitter: float = 0.2,
+                   planar: bool = False) -> np.ndarray:
+    """n atoms drawn without replacement from a jittered cubic (or square) grid:
+    no two atoms closer than (1 - 2 jitter) * spacing.  For tests."""
+    rng = np.random.default_rng(seed)
+    dim = 2 if planar else 3
+    side = int(math.ceil((2.0 * n) ** (1.0 / dim)))
+    grid = np.stack(np.meshgrid(*[np.arange(side)] * dim, indexing="ij"), axis=-1).reshape(-1, dim)
+    pick = rng.choice(len(grid), size=n, replace=False)
+    pts = grid[pick].astype(np.float64) + rng.uniform(-jitter, jitter, size=(n, dim))
+    pts *= spacing_bohr
+    xyz = np.zeros((n, 3))
+    xyz[:, :dim] = pts
+    xyz -= xyz.mean(axis=0)
+    return xyz
+
+
+def random_complex(shape, seed: int) -> np.ndarray:
+    """Seeded standard complex normal array (apply-only inputs)."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2.0)
+
+
+# --------------------------------------------------------------------------- workloads
+
+def workload(name: str) -> dict:
+    """Named synthetic workloads (positions in bohr, frequencies in hartree).
+
+    flake1k   hexagonal zigzag graphene flake, 13 rings, N = 1014; one frequency at
+              the flake's dipolar resonance (0.52 eV with carbon_params(1.51)); x
+    cnt20k    armchair (10,10) nanotube, 500 cells, N = 20000; 64 frequencies evenly
+              over 0.05-2.0 eV; directions x, y, z
+    sphere150k fcc sphere a = 4.23 A, ~150k atoms, surface jitter +-0.05 A; 32
+              frequencies over 0.9-1.8 eV; x, y, z
+    disk1m    graphene disk with ~1.01M sites, 1% vacancies; 16 frequencies over
+              0.05-0.20 eV; direction x
+    """
+    dirs3 = np.eye(3)
+    if name == "flake1k":
+        return {"xyz": honeycomb_flake(13), "params": carbon_params(1.51),
+                "omega": ev([0.52]), "dirs": dirs3[:1]}
+    if name == "cnt20k":
+        return {"xyz": nanotube(10, 10, 500), "params": carbon_params(1.04),
+                "omega": ev(np.linspace(0.05, 2.0, 64)), "dirs": dirs3}
+    if name == "sphere150k":
+        a = 4.23
+        R = fcc_sphere_radius_for(150_000, a)
+        return {"xyz": fcc_sphere(a, R, 0.05, seed=20210301), "params": sodium_params(),
+                "omega": ev(np.linspace(0.9, 1.8, 32)), "dirs": dirs3}
+    if name == "disk1m":
+        return {"xyz": graphene_disk(183.58, vacancy_frac=0.01, seed=20210304),
+                "params": carbon_params(1.84),
+                "omega": ev(np.linspace(0.05, 0.20, 16)), "dirs": dirs3[:1]}
+    raise KeyError(name)
