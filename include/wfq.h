@@ -1,0 +1,211 @@
+/*
+ * wfq.h -- C ABI of libwfq, the GB300 (sm_103a) implementation of the omega-FQ
+ * frequency-dependent charge-response solve of arXiv 2103.00438.
+ *
+ * The method (Section 2.1): for N atoms at positions r_i, the complex charges q
+ * at frequency w under a uniform field E0 along k solve
+ *
+ *     (A - z(w) I) q = R                                     (Eq. 14)
+ *     A = (Kbar - P) D                                       (Eq. 17)
+ *     D_ij = erf(r_ij / sqrt(w_i^2 + w_j^2)) / r_ij, D_ii = eta_i,
+ *            w_i = sqrt(2/pi) / eta_i                        (Eq. 3, Eq. 4)
+ *     Kbar_ij = (1 - f(r_ij)) area / r_ij, Kbar_ii = 0,
+ *            f(r) = 1 / (1 + exp(-d (r / (s r0) - 1)))       (Eq. 9, Eq. 6)
+ *     P = diag(sum_k Kbar_ik)                                (Eq. 16)
+ *     z(w) = -(w / (2 n0 tau)) (w tau + i)                   (Eq. 12)
+ *     R_i = sum_j (V_i - V_j) Kbar_ij, V_i = -E0 (r_i . k)   (Eq. 13, Eq. 2)
+ *
+ * Units are atomic units throughout (bohr, hartree, a.u. of time).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: WFQ_OK (0) or a negative WFQ_E* code.
+ *     Nothing throws across the ABI.  wfq_last_error() returns a message for the
+ *     last failure on the calling thread.
+ *   - The caller owns every array it passes; the library owns the handles it
+ *     creates and all device memory inside them.
+ *   - Complex arrays are interleaved (re, im) doubles (complex128) or floats
+ *     (complex64).  A "block" of ncols complex vectors of length N is stored
+ *     atom-major: element (atom i, column c) at index i * ncols + c.
+ *   - Array pointers may be host or device pointers unless stated otherwise; the
+ *     library tells them apart with cudaPointerGetAttributes.  Host buffers are
+ *     staged through device memory inside the call.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     queued on it.  Calls that return host-visible results (solves, stats,
+ *     host output buffers) synchronise that stream before returning.
+ *   - One wfq_ctx per device; handles may be used from one thread at a time.
+ */
+#ifndef WFQ_H
+#define WFQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+    WFQ_OK = 0,
+    WFQ_EINVAL = -1,       /* bad argument: shape, NaN/Inf, non-positive parameter,
+                              two atoms at the same position (r_ij = 0) */
+    WFQ_ESINGULAR = -2,    /* omega = 0: z = 0 and A is singular (Section 2.1) */
+    WFQ_ENOMEM = -3,       /* device allocation failed or the request exceeds the
+                              context's memory budget */
+    WFQ_ENOCONV = -4,      /* iteration limit reached; best iterate written, stats filled */
+    WFQ_EBREAKDOWN = -5,   /* QMR without look-ahead met rho = 0 or sigma = 0 */
+    WFQ_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
+    WFQ_ECUDA = -7,        /* CUDA runtime error (message in wfq_last_error) */
+    WFQ_EUNSUPPORTED = -8  /* combination not available (e.g. mixed apply without the
+                              bf16 D storage) */
+};
+
+typedef struct wfq_ctx wfq_ctx;
+typedef struct wfq_geom wfq_geom;
+
+/* Model parameters (atomic units).  Section 2 / Eqs. 3-12. */
+typedef struct {
+    double eta;        /* chemical hardness eta_i (Eq. 3 diagonal) when no per-atom array */
+    double d_fermi;    /* steepness d of the Fermi damping (Eq. 6) */
+    double s_fermi;    /* scale s of the Fermi damping (Eq. 6) */
+    double r0;         /* equilibrium distance r0_ij (Eq. 6), uniform, bohr */
+    double area;       /* effective area A_ij (Eq. 5 / Eq. 9), uniform */
+    double n0;         /* electron density n0; the Drude factor is 2 n0 (Eq. 12) */
+    double tau;        /* relaxation time tau (Eq. 5 / Eq. 12) */
+    double cutoff_eps; /* Kbar keeps pair (i,j) iff 1 - f(r_ij) >= cutoff_eps; 0 keeps all */
+} wfq_params;
+
+/* Storage of D chosen at geometry build (bit flags).  With no flag set D is never
+ * stored: every apply recomputes its entries from the coordinates (matrix-free). */
+#define WFQ_STORE_FP64   1u  /* D in FP64, N*N*8 bytes: FP64 applies and residuals */
+#define WFQ_STORE_BF16X2 2u  /* D as two bf16 planes hi + lo (D ~= hi + lo), Np*Np*4 bytes
+                                with Np = N rounded up to 128: the tensor-core path */
+
+/* Arithmetic of an apply / of the inner Krylov iterations. */
+enum {
+    WFQ_PREC_FP64 = 0,     /* FP64 operator, complex128 vectors */
+    WFQ_PREC_MIXED = 1     /* D.x from 3 bf16 products (hi.hi + hi.lo + lo.hi) with FP32
+                              accumulation, complex64 vectors; solves add FP64 iterative
+                              refinement on top */
+};
+
+/* Per-solve statistics. */
+typedef struct {
+    int32_t iters;        /* operator applications inside Krylov iterations */
+    int32_t restarts;     /* restart cycles after the first (GMRES) */
+    int32_t refinements;  /* FP64 true-residual evaluations after the first cycle */
+    int32_t status;       /* WFQ_OK, WFQ_ENOCONV or WFQ_EBREAKDOWN */
+    double rel_residual;  /* ||R - (A - zI) q||_2 / ||R||_2, FP64 (Eq. 27 / ||R||) */
+    double rmse;          /* ||R - (A - zI) q||_2 / sqrt(N)  (Eq. 33) */
+} wfq_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device`.  *ctx is set on success. */
+int wfq_create(wfq_ctx **ctx, int device);
+
+/* Releases the context.  Geometries created on it must be freed first. */
+int wfq_destroy(wfq_ctx *ctx);
+
+/* Message of the last failure on this thread ("" if none).  Owned by the library. */
+const char *wfq_last_error(void);
+
+/* Number of CUDA kernels libwfq has launched in this process so far (all threads).
+ * Profiling aid: the difference across a region counts the library's launches in it. */
+int64_t wfq_kernel_launches(void);
+
+/* Kernel timing (profiling aid).  While enabled, the library records a pair of CUDA
+ * events on the launching stream around every launch of the kernels below;
+ * wfq_profile_read synchronises those events and returns the launch count and the
+ * summed device time since the last wfq_profile(ctx, 1) call. */
+enum {
+    WFQ_KT_GEMM_MIXED = 0,   /* 3xBF16 tensor-core GEMM  U = D X   (mixed apply) */
+    WFQ_KT_DAPPLY_FP64 = 1,  /* FP64 dense product U = D X (stored or recomputed D) */
+    WFQ_KT_SPARSE = 2,       /* sparse term and shift  Y = Kbar U - P U - z X */
+    WFQ_KT_COUNT = 3
+};
+
+/* enable != 0: reset the counters and start recording; enable == 0: stop. */
+int wfq_profile(wfq_ctx *ctx, int enable);
+
+/* Launches and summed device milliseconds of kernel class `kind` (WFQ_KT_*). */
+int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms);
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Builds everything that depends only on the structure (Section 2.1: A and R do
+ * not depend on omega):
+ *   - per-atom data (positions, Gaussian widths from Eq. 4),
+ *   - Kbar as CSR with a cell-list neighbour search (pairs with
+ *     1 - f(r) >= cutoff_eps, Eq. 9) and P (Eq. 16),
+ *   - D (Eq. 3) in the storages requested by `store` (WFQ_STORE_* flags).
+ * xyz: host, n x 3 row-major bohr.  eta: host array of n hardnesses or NULL (then
+ * p->eta for every atom).  Fails with WFQ_EINVAL for n < 1, non-finite input,
+ * non-positive eta/d/s/r0/area/n0/tau, cutoff_eps outside [0, 1), or two atoms
+ * closer than 1e-8 bohr.  *out is set on success. */
+int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double *eta,
+                       const wfq_params *p, uint32_t store, wfq_geom **out);
+
+int wfq_free_geometry(wfq_geom *g);
+
+/* n: atoms; nnz: stored Kbar pairs; device_bytes: device memory held by g. */
+int wfq_geometry_info(const wfq_geom *g, int64_t *n, int64_t *nnz, int64_t *device_bytes);
+
+/* ---------------------------------------------------------------- operator */
+
+/* y = (A - z(omega_c) I) x for ncplx complex columns (Eq. 14's operator, applied
+ * through the factored form of Eq. 17):  u = D x,  y = Kbar u - P u - z x.
+ * omega: host array of ncplx frequencies (hartree), one per column; omega_c = 0 is
+ * allowed here (z = 0).  x, y: N x ncplx atom-major blocks, complex128 for
+ * WFQ_PREC_FP64 and complex64 for WFQ_PREC_MIXED; x and y must not overlap.
+ * FP64 uses the stored FP64 D if present, else recomputes D (matrix-free).
+ * MIXED needs WFQ_STORE_BF16X2 (else WFQ_EUNSUPPORTED).  Asynchronous on `stream`
+ * when x and y are device pointers. */
+int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, void *y,
+              int prec, void *stream);
+
+/* Right-hand sides R (Eq. 13 with the potential of Eq. 2) for ndir field
+ * directions.  dirs: host, ndir x 3 (need not be unit vectors; the field is E0 * dir).
+ * R: N x ndir atom-major real (FP64). */
+int wfq_rhs(wfq_geom *g, int ndir, const double *dirs, double E0, double *R, void *stream);
+
+/* ---------------------------------------------------------------- solvers */
+
+/* Solves (A - z(omega_f) I) q = R(dir_d) for every frequency f < nfreq and field
+ * direction d < ndir at once (ncols = nfreq * ndir complex columns sharing D and
+ * Kbar; column c = f * ndir + d), by GMRES (Section 3, Eq. 24) from q0 = 0.
+ *   m: restart length (GMRES(m)); 0 = unrestarted (one cycle of up to max_iter).
+ *   rel_tol: stop when the FP64 true residual satisfies ||R - (A - zI) q|| <= rel_tol ||R||
+ *            for every column (Eq. 27 relative to ||R||).
+ *   max_iter: cap on Krylov iterations per column.
+ *   prec: WFQ_PREC_FP64 -- FP64 operator and complex128 Krylov basis;
+ *         WFQ_PREC_MIXED -- each restart cycle iterates with the mixed operator and a
+ *         complex64 basis (FP64 inner products, norms and Givens rotations); every cycle
+ *         starts from the FP64 true residual (iterative refinement).
+ * q: output, N x ncols complex128 atom-major.  stats: host array of ncols, or NULL.
+ * Returns WFQ_OK when every column converged, WFQ_ENOCONV otherwise (q holds the last
+ * iterate), WFQ_ESINGULAR if some omega is 0.  Synchronises `stream`. */
+int wfq_solve_gmres(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
+                    const double *dirs, double E0, int m, double rel_tol, int max_iter,
+                    int prec, double *q, wfq_stats *stats, void *stream);
+
+/* As wfq_solve_gmres, with the J-symmetric QMR-from-BCG method without look-ahead
+ * (Section 3; J = D since D A = A^T D, Eq. 18).  The bilinear form u^T D v needs D v,
+ * which the operator apply already produces, so each iteration costs one D product.
+ * With WFQ_PREC_MIXED the QMR recurrence restarts from the FP64 true residual every
+ * `refine_every` iterations (0 = only when its own residual estimate converges).
+ * Returns WFQ_EBREAKDOWN if rho or sigma vanishes in some column. */
+int wfq_solve_qmr(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
+                  const double *dirs, double E0, double rel_tol, int max_iter, int prec,
+                  int refine_every, double *q, wfq_stats *stats, void *stream);
+
+/* Complex polarizability of each solved column: alpha[c][k'] = sum_i q_i r_{i,k'} / E0
+ * for k' = x, y, z (Section 4.1, Eq. 28: sigma_k = (4 pi w / c) Im alpha_kk).
+ * q: N x ncols complex128 (host or device).  alpha: host, ncols x 3 complex128. */
+int wfq_polarizability(wfq_geom *g, int64_t ncols, const double *q, double E0,
+                       double *alpha, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WFQ_H */

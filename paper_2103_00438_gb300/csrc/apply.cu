@@ -1,0 +1,398 @@
+// Pieces of the operator apply y = (A - zI) x through the factored form of Eq. 17:
+//   u = D x              (dense; FP64 stored / FP64 recomputed / 3xBF16 tensor cores)
+//   y = Kbar u - P u - z x   (sparse neighbour term of Eq. 16-17 plus the shift of Eq. 14)
+// Block vectors are atom-major: (atom i, complex column c) at i * cc + c.
+#include "common.h"
+
+namespace wfq {
+
+// ------------------------------------------------------------------ FP64 stored D: few columns
+
+// U[i][:] = sum_k D[i][k] X[k][:] for C real columns (C <= 8): each warp owns 4 rows so
+// that every X element read from L2 serves 4 D rows; D rows are read coalesced.
+template <int C>
+__global__ void __launch_bounds__(256) k_dgemv(int64_t n, const double *__restrict__ D,
+                                               const double *__restrict__ X, double *__restrict__ U) {
+    constexpr int RW = 4;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    int64_t i0 = warp * RW;
+    if (i0 >= n) return;
+    double acc[RW][C];
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[r][c] = 0.0;
+    const double *rows[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) rows[r] = D + min(i0 + r, n - 1) * n;
+    int64_t k = lane;
+    for (; k + 96 < n; k += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            int64_t kk = k + 32 * u;
+            double x[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) x[c] = __ldg(X + kk * C + c);
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                double d = __ldcs(rows[r] + kk);
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[r][c] = fma(d, x[c], acc[r][c]);
+            }
+        }
+    }
+    for (; k < n; k += 32) {
+        double x[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) x[c] = __ldg(X + k * C + c);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            double d = __ldcs(rows[r] + k);
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[r][c] = fma(d, x[c], acc[r][c]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            double v = acc[r][c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc[r][c] = v;
+        }
+    if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+            if (i0 + r < n)
+#pragma unroll
+                for (int c = 0; c < C; ++c) U[(i0 + r) * C + c] = acc[r][c];
+    }
+}
+
+// ------------------------------------------------------------------ FP64 stored D: many columns
+
+// U[n x C] = D[n x n] X[n x C], row-major, 64 x 64 tiles, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) k_dgemm(int64_t n, int64_t C, const double *__restrict__ D,
+                                               const double *__restrict__ X, double *__restrict__ U) {
+    __shared__ double As[16][65];
+    __shared__ double Bs[16][64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    double acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < n; k0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            int e = tid + l * 256;
+            int r = e >> 4, kk = e & 15;
+            int64_t gi = m0 + r, gk = k0 + kk;
+            As[kk][r] = (gi < n && gk < n) ? D[gi * n + gk] : 0.0;
+            int kb = e >> 6, cb = e & 63;
+            int64_t bk = k0 + kb, bc = n0 + cb;
+            Bs[kb][cb] = (bk < n && bc < C) ? X[bk * C + bc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                a[t] = As[kk][ty * 4 + t];
+                b[t] = Bs[kk][tx * 4 + t];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int64_t gi = m0 + ty * 4 + r;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int64_t gc = n0 + tx * 4 + c;
+            if (gc < C) U[gi * C + gc] = acc[r][c];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ FP64 matrix-free D
+
+__device__ __forceinline__ double d_pair64(atom64_t a, atom64_t b) {
+    double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double r = sqrt(r2);
+    double s2 = a.w * a.w + b.w * b.w;
+    if (r2 >= 36.0 * s2) return 1.0 / r;   // erf(r/sigma) == 1 in FP64 here
+    return erf(r / sqrt(s2)) / r;
+}
+
+// As k_dgemm, with the D tile (Eq. 3) recomputed from the coordinates for every use.
+__global__ void __launch_bounds__(256) k_dotf(int64_t n, int64_t C, const atom64_t *__restrict__ atom,
+                                              const double *__restrict__ eta,
+                                              const double *__restrict__ X, double *__restrict__ U) {
+    __shared__ double As[16][65];
+    __shared__ double Bs[16][64];
+    __shared__ atom64_t Ai[64];
+    __shared__ double Ei[64];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+    if (tid < 64) {
+        int64_t gi = min(m0 + tid, n - 1);
+        Ai[tid] = atom[gi];
+        Ei[tid] = eta[gi];
+    }
+    __syncthreads();
+    double acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < n; k0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            int e = tid + l * 256;
+            int r = e & 63, kk = e >> 6;
+            int64_t gi = m0 + r, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < n && gk < n) v = (gi == gk) ? Ei[r] : d_pair64(Ai[r], atom[gk]);
+            As[kk][r] = v;
+            int kb = e >> 6, cb = e & 63;
+            int64_t bk = k0 + kb, bc = n0 + cb;
+            Bs[kb][cb] = (bk < n && bc < C) ? X[bk * C + bc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                a[t] = As[kk][ty * 4 + t];
+                b[t] = Bs[kk][tx * 4 + t];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int64_t gi = m0 + ty * 4 + r;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int64_t gc = n0 + tx * 4 + c;
+            if (gc < C) U[gi * C + gc] = acc[r][c];
+        }
+    }
+}
+
+int d_apply_fp64(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
+    const int64_t n = g->n, C = 2 * cc;
+    const double *x = reinterpret_cast<const double *>(X);
+    double *u = reinterpret_cast<double *>(U);
+    KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s);
+    if (g->D64 && C <= 8) {
+        int64_t warps = (n + 3) / 4;
+        unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+        switch (C) {
+            case 2: k_dgemv<2><<<blocks, 256, 0, s>>>(n, g->D64, x, u); note_launch(); break;
+            case 4: k_dgemv<4><<<blocks, 256, 0, s>>>(n, g->D64, x, u); note_launch(); break;
+            case 6: k_dgemv<6><<<blocks, 256, 0, s>>>(n, g->D64, x, u); note_launch(); break;
+            default: k_dgemv<8><<<blocks, 256, 0, s>>>(n, g->D64, x, u); note_launch(); break;
+        }
+    } else {
+        dim3 grid((unsigned)((C + 63) / 64), (unsigned)((n + 63) / 64));
+        if (grid.y > 65535u) return fail(WFQ_EUNSUPPORTED, "FP64 apply: too many rows");
+        if (g->D64) {
+            k_dgemm<<<grid, 256, 0, s>>>(n, C, g->D64, x, u);
+        } else {
+            k_dotf<<<grid, 256, 0, s>>>(n, C, g->atom64, g->eta, x, u);
+        }
+        note_launch();
+    }
+    WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
+}
+
+// ------------------------------------------------------------------ sparse term + shift
+
+template <class V>
+struct CplxT;
+template <>
+struct CplxT<double2> {
+    using R = double;
+};
+template <>
+struct CplxT<float2> {
+    using R = float;
+};
+
+// Many columns: one warp per atom row, lanes over complex columns.
+// Y_i = sum_p Kbar_ip (U_j - U_i) - z X_i  (the difference form of Kbar U - P U).
+template <class V, class VAL>
+__global__ void __launch_bounds__(128) k_sparse_cols(int64_t n, int64_t cc,
+                                                     const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col,
+                                                     const VAL *__restrict__ val,
+                                                     const V *__restrict__ U, const V *__restrict__ X,
+                                                     const double2 *__restrict__ z, V *__restrict__ Y) {
+    using R = typename CplxT<V>::R;
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
+    for (int64_t c = lane; c < cc; c += 32) {
+        V ui = U[i * cc + c];
+        R ax = 0, ay = 0;
+        for (int64_t p = p0; p < p1; ++p) {
+            R w = (R)val[p];
+            V uj = U[(int64_t)col[p] * cc + c];
+            ax += w * (uj.x - ui.x);
+            ay += w * (uj.y - ui.y);
+        }
+        V xv = X[i * cc + c];
+        double2 zc = z[c];
+        R zr = (R)zc.x, zi = (R)zc.y;
+        V out;
+        out.x = ax - (zr * xv.x - zi * xv.y);
+        out.y = ay - (zr * xv.y + zi * xv.x);
+        Y[i * cc + c] = out;
+    }
+}
+
+// Few columns (cc <= 4): one warp per atom row, lanes over neighbours.
+template <class V, class VAL, int CC>
+__global__ void __launch_bounds__(128) k_sparse_nbrs(int64_t n, const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col,
+                                                     const VAL *__restrict__ val,
+                                                     const V *__restrict__ U, const V *__restrict__ X,
+                                                     const double2 *__restrict__ z, V *__restrict__ Y) {
+    using R = typename CplxT<V>::R;
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
+    V ui[CC];
+    R ax[CC], ay[CC];
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+        ui[c] = U[i * CC + c];
+        ax[c] = 0;
+        ay[c] = 0;
+    }
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+        R w = (R)val[p];
+        int64_t j = col[p];
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+            V uj = U[j * CC + c];
+            ax[c] += w * (uj.x - ui[c].x);
+            ay[c] += w * (uj.y - ui[c].y);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ax[c] += __shfl_xor_sync(0xffffffffu, ax[c], o);
+            ay[c] += __shfl_xor_sync(0xffffffffu, ay[c], o);
+        }
+    }
+    if (lane < CC) {
+        // lane c writes column c
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+            if (c != lane) continue;
+            V xv = X[i * CC + c];
+            double2 zc = z[c];
+            R zr = (R)zc.x, zi = (R)zc.y;
+            V out;
+            out.x = ax[c] - (zr * xv.x - zi * xv.y);
+            out.y = ay[c] - (zr * xv.y + zi * xv.x);
+            Y[i * CC + c] = out;
+        }
+    }
+}
+
+template <class V, class VAL>
+static int sparse_shift_impl(const wfq_geom *g, int64_t cc, const V *U, const V *X, const double2 *z,
+                             V *Y, const VAL *val, cudaStream_t s) {
+    const int64_t n = g->n;
+    unsigned blocks = (unsigned)((n * 32 + 127) / 128);
+    KScope ks(g->ctx, WFQ_KT_SPARSE, s);
+    switch (cc) {
+        case 1: k_sparse_nbrs<V, VAL, 1><<<blocks, 128, 0, s>>>(n, g->rowptr, g->col, val, U, X, z, Y); note_launch(); break;
+        case 2: k_sparse_nbrs<V, VAL, 2><<<blocks, 128, 0, s>>>(n, g->rowptr, g->col, val, U, X, z, Y); note_launch(); break;
+        case 3: k_sparse_nbrs<V, VAL, 3><<<blocks, 128, 0, s>>>(n, g->rowptr, g->col, val, U, X, z, Y); note_launch(); break;
+        case 4: k_sparse_nbrs<V, VAL, 4><<<blocks, 128, 0, s>>>(n, g->rowptr, g->col, val, U, X, z, Y); note_launch(); break;
+        default:
+            k_sparse_cols<V, VAL><<<blocks, 128, 0, s>>>(n, cc, g->rowptr, g->col, val, U, X, z, Y); note_launch();
+    }
+    WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
+}
+
+int sparse_shift_fp64(const wfq_geom *g, int64_t cc, const double2 *U, const double2 *X,
+                      const double2 *z, double2 *Y, cudaStream_t s) {
+    return sparse_shift_impl<double2, double>(g, cc, U, X, z, Y, g->val64, s);
+}
+
+int sparse_shift_fp32(const wfq_geom *g, int64_t cc, const float2 *U, const float2 *X,
+                      const double2 *z, float2 *Y, cudaStream_t s) {
+    return sparse_shift_impl<float2, float>(g, cc, U, X, z, Y, g->val32, s);
+}
+
+// ------------------------------------------------------------------ mixed: split + GEMM
+
+// X: n x (2 cc) real view (complex64 atom-major) -> Xhi/Xlo: [cpad][npad] bf16 (K-major
+// operand of the GEMM), hi = bf16(x), lo = bf16(x - hi); zero padding.
+__global__ void __launch_bounds__(256) k_split_bf16(int64_t n, int64_t npad, int64_t C, int64_t cpad,
+                                                    const float *__restrict__ X,
+                                                    __nv_bfloat16 *__restrict__ hi,
+                                                    __nv_bfloat16 *__restrict__ lo) {
+    __shared__ float t[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t a0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        int64_t a = a0 + r, c = c0 + tx;
+        t[r][tx] = (a < n && c < C) ? X[a * C + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = ty; r < 32; r += 8) {
+        int64_t c = c0 + r, a = a0 + tx;
+        if (c < cpad && a < npad) {
+            float v = t[tx][r];
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+            hi[c * npad + a] = h;
+            lo[c * npad + a] = l;
+        }
+    }
+}
+
+// Rows of the bf16 X planes: the real columns rounded up to whole 64-column GEMM tiles.
+static int64_t mixed_cpad(int64_t cc) { return round_up(2 * cc, 64); }
+
+size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc) {
+    int64_t cpad = mixed_cpad(cc);
+    return (size_t)2 * cpad * g->npad * sizeof(__nv_bfloat16);
+}
+
+int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
+                  cudaStream_t s) {
+    if (!g->Dhi) return fail(WFQ_EUNSUPPORTED, "mixed apply needs WFQ_STORE_BF16X2");
+    const int64_t C = 2 * cc, cpad = mixed_cpad(cc), npad = g->npad;
+    __nv_bfloat16 *xhi = reinterpret_cast<__nv_bfloat16 *>(scratch);
+    __nv_bfloat16 *xlo = xhi + cpad * npad;
+    dim3 grid((unsigned)(npad / 32), (unsigned)((cpad + 31) / 32));
+    k_split_bf16<<<grid, 256, 0, s>>>(g->n, npad, C, cpad, reinterpret_cast<const float *>(X), xhi, xlo); note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    return gemm_3xbf16(g, cpad, xhi, xlo, reinterpret_cast<float *>(U), C, s);
+}
+
+}  // namespace wfq

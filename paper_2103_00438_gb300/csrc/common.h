@@ -1,0 +1,216 @@
+// Internal declarations of libwfq (not part of the C ABI; see include/wfq.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/wfq.h"
+
+namespace wfq {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string &msg);
+const char *get_error();
+
+struct Status {
+    int code = WFQ_OK;
+    explicit operator bool() const { return code != WFQ_OK; }
+};
+
+#define WFQ_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ::wfq::set_error(std::string(#call) + ": " + cudaGetErrorString(e_) + " at " + \
+                             __FILE__ + ":" + std::to_string(__LINE__));                   \
+            return WFQ_ECUDA;                                                              \
+        }                                                                                  \
+    } while (0)
+
+#define WFQ_TRY(expr)                 \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != WFQ_OK) return rc_; \
+    } while (0)
+
+inline int fail(int code, const std::string &msg) {
+    set_error(msg);
+    return code;
+}
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ------------------------------------------------------------------ handles
+
+// Tensor-core tile geometry of the stored bf16 D planes: rows and columns padded
+// to a multiple of kTilePad with zero entries.
+constexpr int64_t kTilePad = 128;
+
+// Per-atom record for the FP64 kernels: position and Gaussian width (Eq. 4).
+struct __align__(32) atom64_t {
+    double x, y, z, w;
+};
+
+}  // namespace wfq
+
+namespace wfq {
+
+// Event-pair timing of selected kernel classes (wfq_profile / wfq_profile_read).
+struct KernelTimer {
+    std::mutex mu;
+    bool enabled = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[WFQ_KT_COUNT];
+    std::vector<cudaEvent_t> pool;
+    int64_t launches[WFQ_KT_COUNT] = {};
+    double ms[WFQ_KT_COUNT] = {};
+    cudaEvent_t get();
+    void collect();
+    void reset();
+    ~KernelTimer();
+};
+
+}  // namespace wfq
+
+struct wfq_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaMemPool_t pool = nullptr;
+    wfq::KernelTimer timer;
+};
+
+struct wfq_geom {
+    wfq_ctx *ctx = nullptr;
+    int64_t n = 0;      // atoms
+    int64_t npad = 0;   // n rounded up to kTilePad (bf16 plane dimension)
+    wfq_params p{};
+    uint32_t store = 0;
+    int64_t nnz = 0;
+    size_t bytes = 0;   // device bytes held
+
+    // per-atom (device)
+    double *xyz = nullptr;      // n x 3
+    wfq::atom64_t *atom64 = nullptr;  // (x, y, z, width), n
+    float4 *atom32 = nullptr;   // (x, y, z, width), npad (padding: far away, width 1)
+    double *eta = nullptr;      // n
+
+    // Kbar CSR (device)
+    int64_t *rowptr = nullptr;  // n + 1
+    int32_t *col = nullptr;     // nnz
+    double *val64 = nullptr;    // nnz
+    float *val32 = nullptr;     // nnz
+
+    // D storages (device)
+    double *D64 = nullptr;      // n x n row-major (ld = n)
+    __nv_bfloat16 *Dhi = nullptr;  // npad x npad row-major
+    __nv_bfloat16 *Dlo = nullptr;
+};
+
+namespace wfq {
+
+// ------------------------------------------------------------------ memory
+
+// Stream-ordered allocation from the context's pool.
+int dalloc(wfq_ctx *ctx, void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+
+template <class T>
+struct DevBuf {
+    T *ptr = nullptr;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() {
+        if (ptr) dfree(ptr, s);
+    }
+    int alloc(wfq_ctx *ctx, size_t count, cudaStream_t stream) {
+        s = stream;
+        return dalloc(ctx, reinterpret_cast<void **>(&ptr), count * sizeof(T), stream);
+    }
+};
+
+// Counts kernel launches made by the library (wfq_kernel_launches).
+void note_launch();
+
+// Records start/end events around the launches made in its scope when timing is on.
+struct KScope {
+    wfq_ctx *ctx;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr;
+    KScope(wfq_ctx *c, int k, cudaStream_t st);
+    ~KScope();
+};
+
+// True if p is a device (or managed) pointer usable by kernels.
+bool is_device_ptr(const void *p);
+
+// ------------------------------------------------------------------ geometry build
+
+int build_kbar_csr(int64_t n, const double *xyz, const wfq_params &p, std::vector<int64_t> &rowptr,
+                   std::vector<int32_t> &col, std::vector<double> &val);
+
+int launch_build_d(const wfq_geom *g, cudaStream_t s);
+int launch_rhs(const wfq_geom *g, int ndir, const double *dirs_dev, double E0, double *R,
+               cudaStream_t s);
+int launch_polarizability(const wfq_geom *g, int64_t ncols, const double2 *q, double E0,
+                          double2 *alpha_dev, cudaStream_t s);
+
+// ------------------------------------------------------------------ operator pieces
+// Block vectors are atom-major: element (atom i, complex column c) at i * cc + c.
+
+// U = D X in FP64 (stored FP64 D if present, else recomputed from the coordinates).
+int d_apply_fp64(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s);
+
+// U = D X with 3 bf16 products and FP32 accumulation (stored bf16 planes).
+// scratch: at least mixed_scratch_bytes(g, cc) bytes of device memory.
+size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc);
+int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
+                  cudaStream_t s);
+
+// Y = Kbar U - P U - z_c X   (z: device, cc values)
+int sparse_shift_fp64(const wfq_geom *g, int64_t cc, const double2 *U, const double2 *X,
+                      const double2 *z, double2 *Y, cudaStream_t s);
+int sparse_shift_fp32(const wfq_geom *g, int64_t cc, const float2 *U, const float2 *X,
+                      const double2 *z, float2 *Y, cudaStream_t s);
+
+// U[n x ldu] (fp32, row-major) = Dhi.Xhi + Dhi.Xlo + Dlo.Xhi where Xhi/Xlo are
+// [cpad x npad] bf16 (K-major), cpad a multiple of 64 and >= ldu.  Only rows < n and
+// columns < ldu of U are written.
+int gemm_3xbf16(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi,
+                const __nv_bfloat16 *Xlo, float *U, int64_t ldu, cudaStream_t s);
+
+// ------------------------------------------------------------------ solvers
+
+struct SolveArgs {
+    int64_t nfreq = 0;
+    const double *omega = nullptr;  // host
+    int ndir = 0;
+    const double *dirs = nullptr;   // host, ndir x 3
+    double E0 = 1.0;
+    int m = 0;
+    double rel_tol = 1e-8;
+    int max_iter = 1000;
+    int prec = WFQ_PREC_FP64;
+    int refine_every = 0;
+    double2 *q = nullptr;           // device, n x ncols
+    wfq_stats *stats = nullptr;     // host, ncols (may be null)
+};
+
+int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
+int solve_qmr(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
+
+// z(omega) of Eq. 12 for the geometry's parameters.
+inline double2 z_of_omega(const wfq_params &p, double omega) {
+    double f = -omega / (2.0 * p.n0 * p.tau);
+    return make_double2(f * omega * p.tau, f);
+}
+
+}  // namespace wfq

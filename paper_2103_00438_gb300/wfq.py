@@ -1,0 +1,230 @@
+"""Python binding of libwfq (include/wfq.h): argument marshalling only.
+
+Every computation runs inside libwfq.so.  Arrays may be numpy arrays (host) or
+torch CUDA tensors (device); the library tells host and device pointers apart.
+There is no CPU fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+WFQ_OK = 0
+STATUS = {0: "WFQ_OK", -1: "WFQ_EINVAL", -2: "WFQ_ESINGULAR", -3: "WFQ_ENOMEM", -4: "WFQ_ENOCONV",
+          -5: "WFQ_EBREAKDOWN", -6: "WFQ_ETIMEOUT", -7: "WFQ_ECUDA", -8: "WFQ_EUNSUPPORTED"}
+STORE_FP64, STORE_BF16X2 = 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+
+# every symbol include/wfq.h declares
+EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry", "wfq_free_geometry",
+           "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_qmr",
+           "wfq_polarizability", "wfq_profile", "wfq_profile_read"]
+KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE = 0, 1, 2
+
+
+class WfqError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("eta", "d_fermi", "s_fermi", "r0", "area", "n0", "tau", "cutoff_eps")]
+
+    @classmethod
+    def from_dict(cls, p):
+        return cls(*[float(p[k]) for k, _ in cls._fields_])
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("rmse", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load(path: str | None = None):
+    """Load libwfq.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.build()
+    L = ctypes.CDLL(path)
+    I64, D, INT = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    L.wfq_create.argtypes = [ctypes.POINTER(_P), INT]
+    L.wfq_destroy.argtypes = [_P]
+    L.wfq_last_error.restype = ctypes.c_char_p
+    L.wfq_kernel_launches.restype = ctypes.c_int64
+    L.wfq_build_geometry.argtypes = [_P, I64, _P, _P, ctypes.POINTER(Params), ctypes.c_uint32,
+                                     ctypes.POINTER(_P)]
+    L.wfq_free_geometry.argtypes = [_P]
+    L.wfq_geometry_info.argtypes = [_P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.wfq_apply.argtypes = [_P, I64, _P, _P, _P, INT, _P]
+    L.wfq_rhs.argtypes = [_P, INT, _P, D, _P, _P]
+    L.wfq_solve_gmres.argtypes = [_P, I64, _P, INT, _P, D, INT, D, INT, INT, _P, _P, _P]
+    L.wfq_solve_qmr.argtypes = [_P, I64, _P, INT, _P, D, D, INT, INT, INT, _P, _P, _P]
+    L.wfq_polarizability.argtypes = [_P, I64, _P, D, _P, _P]
+    L.wfq_profile.argtypes = [_P, INT]
+    L.wfq_profile_read.argtypes = [_P, INT, ctypes.POINTER(I64), ctypes.POINTER(D)]
+    for name in EXPORTS:
+        if name not in ("wfq_last_error", "wfq_kernel_launches"):
+            getattr(L, name).restype = INT
+    _lib = L
+    return L
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libwfq in this process so far."""
+    return int(load().wfq_kernel_launches())
+
+
+def _check(rc, allow=()):
+    if rc != WFQ_OK and rc not in allow:
+        msg = _lib.wfq_last_error().decode(errors="replace")
+        raise WfqError(rc, msg)
+    return rc
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or a torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _host_f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        L = load()
+        h = _P()
+        _check(L.wfq_create(ctypes.byref(h), int(device)))
+        self.h = h
+        self.device = device
+
+    def profile(self, enable: bool):
+        """Start (reset) or stop the library's kernel timers."""
+        _check(_lib.wfq_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, kind: int):
+        """(launches, total device ms) of a kernel class since profile(True)."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        _check(_lib.wfq_profile_read(self.h, int(kind), ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def close(self):
+        if self.h:
+            _check(_lib.wfq_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Geometry:
+    """One structure on the device (wfq_build_geometry)."""
+
+    def __init__(self, ctx: Context, xyz, params: dict, eta=None, store: int = STORE_FP64):
+        xyz = _host_f64(xyz)
+        if xyz.ndim != 2 or xyz.shape[1] != 3:
+            raise ValueError("xyz must be (n, 3)")
+        self.ctx = ctx
+        self.n = len(xyz)
+        self.params = dict(params)
+        self._xyz = xyz
+        eta_a = None if eta is None else _host_f64(eta)
+        p = Params.from_dict(params)
+        h = _P()
+        _check(_lib.wfq_build_geometry(ctx.h, self.n, _ptr(xyz), _ptr(eta_a), ctypes.byref(p), int(store),
+                                       ctypes.byref(h)))
+        self.h = h
+
+    def info(self):
+        n, nnz, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.wfq_geometry_info(self.h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(b)))
+        return {"n": n.value, "nnz": nnz.value, "device_bytes": b.value}
+
+    def close(self):
+        if self.h:
+            _check(_lib.wfq_free_geometry(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- calls
+
+    def apply(self, omega, x, y, prec: int = PREC_FP64, stream=None):
+        """y = (A - z(omega_c) I) x; x, y: (n, ncplx) complex128 (FP64) / complex64 (MIXED)."""
+        om = _host_f64(np.atleast_1d(omega))
+        _check(_lib.wfq_apply(self.h, len(om), _ptr(om), _ptr(x), _ptr(y), int(prec), _stream_handle(stream)))
+        return y
+
+    def rhs(self, dirs, E0=1.0, out=None, stream=None):
+        d = _host_f64(np.atleast_2d(dirs))
+        if out is None:
+            out = np.empty((self.n, len(d)), dtype=np.float64)
+        _check(_lib.wfq_rhs(self.h, len(d), _ptr(d), float(E0), _ptr(out), _stream_handle(stream)))
+        return out
+
+    def _solve(self, qmr, omega, dirs, E0, m, rel_tol, max_iter, prec, refine_every, out, stream):
+        om = _host_f64(np.atleast_1d(omega))
+        d = _host_f64(np.atleast_2d(dirs))
+        ncols = len(om) * len(d)
+        if out is None:
+            out = np.empty((self.n, ncols), dtype=np.complex128)
+        stats = (Stats * ncols)()
+        if qmr:
+            rc = _lib.wfq_solve_qmr(self.h, len(om), _ptr(om), len(d), _ptr(d), float(E0), float(rel_tol),
+                                    int(max_iter), int(prec), int(refine_every), _ptr(out),
+                                    ctypes.cast(stats, _P), _stream_handle(stream))
+        else:
+            rc = _lib.wfq_solve_gmres(self.h, len(om), _ptr(om), len(d), _ptr(d), float(E0), int(m),
+                                      float(rel_tol), int(max_iter), int(prec), _ptr(out),
+                                      ctypes.cast(stats, _P), _stream_handle(stream))
+        _check(rc, allow=(-4, -5))
+        st = [{"iters": s.iters, "restarts": s.restarts, "refinements": s.refinements,
+               "status": STATUS.get(s.status, s.status), "rel_residual": s.rel_residual, "rmse": s.rmse}
+              for s in stats]
+        return out, st, STATUS[rc]
+
+    def solve_gmres(self, omega, dirs, E0=1.0, m=0, rel_tol=1e-8, max_iter=1000, prec=PREC_FP64,
+                    out=None, stream=None):
+        """q (n, nfreq*ndir) complex128, per-column stats, overall status name."""
+        return self._solve(False, omega, dirs, E0, m, rel_tol, max_iter, prec, 0, out, stream)
+
+    def solve_qmr(self, omega, dirs, E0=1.0, rel_tol=1e-8, max_iter=1000, prec=PREC_FP64, refine_every=0,
+                  out=None, stream=None):
+        return self._solve(True, omega, dirs, E0, 0, rel_tol, max_iter, prec, refine_every, out, stream)
+
+    def polarizability(self, q, E0=1.0, stream=None):
+        """alpha (ncols, 3) complex128 from q (n, ncols) complex128 (host or device)."""
+        ncols = q.shape[1]
+        out = np.empty((ncols, 3), dtype=np.complex128)
+        _check(_lib.wfq_polarizability(self.h, ncols, _ptr(q), float(E0), _ptr(out), _stream_handle(stream)))
+        return out

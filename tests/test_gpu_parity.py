@@ -1,0 +1,328 @@
+"""GPU parity of libwfq against the FP64 CPU oracle (through the C ABI).
+
+Tolerances:
+  * integer / structural results (Kbar pair count): exact.
+  * FP64 operator and FP64 solves: 1e-12 relative (operator), q and alpha to 1e-9 / 1e-10
+    against LU (solution error <= cond * 1e-12 tolerance of the solve).
+  * mixed operator (3 bf16 products, FP32 accumulation): per element,
+        |dy_i| <= TAU_MIXED * (sum_p Kbar_ip (s_i + s_j) + |z| |x_i|),  s = |D| |x|,
+    where TAU_MIXED covers the split error of D and x (each <= 2^-18 relative, three
+    products -> 3 * 2^-18 = 1.1e-5) plus FP32 accumulation over N terms.
+  * mixed solves (FP64 refinement): the acceptance bar -- alpha relative error <= 1e-6 and
+    FP64 true residual <= 1e-8 relative, the residual re-measured by the oracle.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TAU_MIXED = 4e-5
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2103_00438_gb300 import wfq
+    wfq.load()
+    return wfq
+
+
+@pytest.fixture(scope="module")
+def ctx(W):
+    c = W.Context(0)
+    yield c
+    c.close()
+
+
+def _carbon(S, **kw):
+    p = S.carbon_params(1.51)
+    p.update(kw)
+    return p
+
+
+def _oracle_csr(orc, xyz, p):
+    return orc.kbar_csr(xyz, p, cutoff_eps=p["cutoff_eps"])
+
+
+# ----------------------------------------------------------------------------- structure
+
+@pytest.mark.parametrize("n_rings", [3, 7, 13])
+def test_kbar_pair_count_exact(W, ctx, orc, S, n_rings):
+    xyz = S.honeycomb_flake(n_rings)
+    p = _carbon(S)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64)
+    rowptr, col, val = _oracle_csr(orc, xyz, p)
+    assert g.info()["nnz"] == len(col)
+
+
+def test_rhs_matches_oracle(W, ctx, orc, S):
+    xyz = S.random_cluster(777, seed=21)
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=0)
+    dirs = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0], [0.6, 0.8, 0.0]])
+    R = g.rhs(dirs, E0=0.7)
+    csr = _oracle_csr(orc, xyz, p)
+    for d in range(4):
+        ref = orc.rhs_csr(xyz, csr, dirs[d], E0=0.7)
+        assert np.abs(R[:, d] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------- operator
+
+def _oracle_apply(orc, sysm, z, x):
+    return orc.Operator.stored(sysm.D, sysm.csr).apply(z, x)
+
+
+@pytest.mark.parametrize("n,store,ncplx", [(1000, "fp64", 1), (1333, "fp64", 3), (1333, "fp64", 7),
+                                           (1100, "otf", 2), (1100, "otf", 5), (257, "otf", 1)])
+def test_apply_fp64_matches_oracle(W, ctx, orc, S, n, store, ncplx):
+    xyz = S.random_cluster(n, seed=n)
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 if store == "fp64" else 0)
+    sysm = orc.System(xyz, p)
+    om = S.ev(np.linspace(0.2, 1.9, ncplx))
+    x = S.random_complex((n, ncplx), seed=5)
+    y = np.empty_like(x)
+    g.apply(om, x, y, prec=W.PREC_FP64)
+    for c in range(ncplx):
+        ref = _oracle_apply(orc, sysm, sysm.z(om[c]), x[:, c])
+        assert np.abs(y[:, c] - ref).max() <= 1e-12 * np.abs(ref).max(), c
+
+
+def _mixed_bound(sysm, z, x):
+    s = np.abs(sysm.D) @ np.abs(x)
+    K = sysm.K
+    return K @ s + K.sum(axis=1) * s + abs(z) * np.abs(x)
+
+
+@pytest.mark.parametrize("n,ncplx", [(1000, 1), (1337, 3), (2049, 8), (129, 2)])
+def test_apply_mixed_within_derived_bound(W, ctx, orc, S, n, ncplx):
+    xyz = S.random_cluster(n, seed=n + 1)
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_BF16X2)
+    sysm = orc.System(xyz, p)
+    om = S.ev(np.linspace(0.3, 1.5, ncplx))
+    x = S.random_complex((n, ncplx), seed=9).astype(np.complex64)
+    y = np.empty_like(x)
+    g.apply(om, x, y, prec=W.PREC_MIXED)
+    worst = 0.0
+    for c in range(ncplx):
+        z = sysm.z(om[c])
+        xc = x[:, c].astype(np.complex128)
+        ref = _oracle_apply(orc, sysm, z, xc)
+        bound = _mixed_bound(sysm, z, xc)
+        worst = max(worst, float(np.max(np.abs(y[:, c] - ref) / bound)))
+    print("mixed apply: max |dy| / unit bound =", worst)
+    assert worst <= TAU_MIXED
+
+
+def test_apply_device_pointers_and_stream(W, ctx, orc, S):
+    torch = pytest.importorskip("torch")
+    n, ncplx = 900, 4
+    xyz = S.random_cluster(n, seed=31)
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 | W.STORE_BF16X2)
+    om = S.ev([0.4, 0.8, 1.2, 1.6])
+    x = S.random_complex((n, ncplx), seed=3)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        g.apply(om, xd, yd, prec=W.PREC_FP64, stream=st)
+    st.synchronize()
+    yh = np.empty_like(x)
+    g.apply(om, x, yh, prec=W.PREC_FP64)
+    assert np.array_equal(yd.cpu().numpy(), yh)
+
+
+# ----------------------------------------------------------------------------- solves
+
+@pytest.fixture(scope="module")
+def flake(orc, S):
+    wl = S.workload("flake1k")
+    sysm = orc.System(wl["xyz"], wl["params"])
+    om = float(wl["omega"][0])
+    q_lu, _ = sysm.solve(om, np.array([1.0, 0, 0]), method="lu")
+    return wl, sysm, om, q_lu
+
+
+def test_gmres_fp64_flake1k_matches_lu(W, ctx, orc, flake):
+    """The flake1k case: complex128 throughout, unrestarted GMRES to 1e-10, vs LU."""
+    wl, sysm, om, q_lu = flake
+    g = W.Geometry(ctx, wl["xyz"], wl["params"], store=W.STORE_FP64)
+    q, st, status = g.solve_gmres([om], [[1.0, 0, 0]], m=0, rel_tol=1e-10, max_iter=2000, prec=W.PREC_FP64)
+    assert status == "WFQ_OK" and st[0]["rel_residual"] <= 1e-10
+    assert np.linalg.norm(q[:, 0] - q_lu) <= 1e-8 * np.linalg.norm(q_lu)
+    a = g.polarizability(q)[0]
+    a_ref = orc.alpha(wl["xyz"], q_lu)
+    assert np.abs(a - a_ref).max() <= 1e-9 * np.abs(a_ref).max()
+    assert abs(q[:, 0].sum()) <= 1e-10 * np.abs(q[:, 0]).sum()
+
+
+@pytest.mark.parametrize("m", [0, 30])
+def test_gmres_mixed_flake1k_acceptance(W, ctx, orc, flake, m):
+    wl, sysm, om, q_lu = flake
+    g = W.Geometry(ctx, wl["xyz"], wl["params"], store=W.STORE_FP64 | W.STORE_BF16X2)
+    q, st, status = g.solve_gmres([om], [[1.0, 0, 0]], m=m, rel_tol=1e-8, max_iter=2000, prec=W.PREC_MIXED)
+    assert status == "WFQ_OK", st
+    a = g.polarizability(q)[0, 0]
+    a_ref = orc.alpha(wl["xyz"], q_lu)[0]
+    assert abs(a - a_ref) <= 1e-6 * abs(a_ref)
+    z = sysm.z(om)
+    R = sysm.rhs(np.array([1.0, 0, 0])).astype(complex)
+    rr = sysm.operator().residual_norm(z, R, q[:, 0]) / np.linalg.norm(R)
+    assert rr <= 1e-8 and abs(rr - st[0]["rel_residual"]) <= 1e-10
+    print("mixed GMRES stats", st[0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_qmr_flake1k(W, ctx, orc, flake, prec):
+    wl, sysm, om, q_lu = flake
+    g = W.Geometry(ctx, wl["xyz"], wl["params"], store=W.STORE_FP64 | W.STORE_BF16X2)
+    P = W.PREC_FP64 if prec == "fp64" else W.PREC_MIXED
+    q, st, status = g.solve_qmr([om], [[1.0, 0, 0]], rel_tol=1e-10 if prec == "fp64" else 1e-8,
+                                max_iter=3000, prec=P)
+    assert status == "WFQ_OK", st
+    a = g.polarizability(q)[0, 0]
+    a_ref = orc.alpha(wl["xyz"], q_lu)[0]
+    assert abs(a - a_ref) <= (1e-9 if prec == "fp64" else 1e-6) * abs(a_ref)
+    print("QMR", prec, st[0])
+
+
+def test_qmr_iterates_match_oracle_qmr(W, ctx, orc, S):
+    """Same method, two derivations: the GPU's direction-vector QMR recurrence and the
+    oracle's smoothing of BCG iterates agree step by step (FP64, capped iterations)."""
+    xyz = S.honeycomb_flake(6)
+    p = _carbon(S)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64)
+    sysm = orc.System(xyz, p)
+    om = S.ev(0.9)
+    R = sysm.rhs(np.array([1.0, 0, 0])).astype(complex)
+    op = sysm.operator()
+    for k in (1, 2, 5, 9):
+        q, st, status = g.solve_qmr([om], [[1.0, 0, 0]], rel_tol=1e-14, max_iter=k, prec=W.PREC_FP64)
+        qo, info = op.qmr(sysm.z(om), R, rel_tol=1e-300, max_iter=k)
+        assert st[0]["iters"] == k
+        assert np.linalg.norm(q[:, 0] - qo) <= 1e-10 * np.linalg.norm(qo), k
+
+
+def test_gmres_iterates_match_oracle_gmres(W, ctx, orc, S):
+    xyz = S.honeycomb_flake(6)
+    p = _carbon(S)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64)
+    sysm = orc.System(xyz, p)
+    om = S.ev(0.7)
+    R = sysm.rhs(np.array([0, 1.0, 0])).astype(complex)
+    op = sysm.operator()
+    for k in (1, 3, 8):
+        q, st, _ = g.solve_gmres([om], [[0, 1.0, 0]], m=0, rel_tol=1e-14, max_iter=k, prec=W.PREC_FP64)
+        qo, _ = op.gmres(sysm.z(om), R, restart=0, rel_tol=1e-300, max_iter=k)
+        assert np.linalg.norm(q[:, 0] - qo) <= 1e-10 * np.linalg.norm(qo), k
+
+
+def test_batched_columns_each_match_oracle(W, ctx, orc, S):
+    """nfreq x ndir columns in one launch: each column equals its own oracle LU solve."""
+    xyz = S.nanotube(5, 5, 30)          # 600 atoms, axis z
+    p = S.carbon_params(1.04)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 | W.STORE_BF16X2)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.15, 0.6, 1.1, 1.9])
+    dirs = np.eye(3)
+    for prec, tol, atol in ((W.PREC_FP64, 1e-11, 1e-8), (W.PREC_MIXED, 1e-8, 1e-6)):
+        q, st, status = g.solve_gmres(om, dirs, m=40, rel_tol=tol, max_iter=4000, prec=prec)
+        assert status == "WFQ_OK"
+        al = g.polarizability(q)
+        for f in range(4):
+            for d in range(3):
+                c = f * 3 + d
+                q_lu, _ = sysm.solve(om[f], dirs[d], method="lu")
+                a_ref = orc.alpha(xyz, q_lu)
+                assert np.abs(al[c] - a_ref).max() <= atol * np.abs(a_ref).max(), (prec, f, d)
+                assert st[c]["rel_residual"] <= tol
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_edge_single_atom_and_dimer(W, ctx, orc, S):
+    p = _carbon(S)
+    g1 = W.Geometry(ctx, np.zeros((1, 3)), p, store=W.STORE_FP64)
+    q, st, status = g1.solve_gmres([0.02], [[1.0, 0, 0]], prec=W.PREC_FP64)
+    assert status == "WFQ_OK" and np.all(q == 0)
+    a = 3.1
+    xyz = np.array([[0.0, 0, 0], [a, 0, 0]])
+    g2 = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 | W.STORE_BF16X2)
+    om = 0.03
+    q, st, status = g2.solve_gmres([om], [[1.0, 0, 0]], rel_tol=1e-12, prec=W.PREC_FP64)
+    k12 = orc.kbar_entry(a, p)
+    d12 = orc.d_matrix(xyz, p["eta"])[0, 1]
+    ref = k12 * a * a / (2 * k12 * (p["eta"] - d12) + orc.z_of_omega(om, p))
+    assert abs(g2.polarizability(q)[0, 0] - ref) <= 1e-11 * abs(ref)
+
+
+def test_edge_field_normal_to_flake_gives_zero(W, ctx, S):
+    xyz = S.honeycomb_flake(4)
+    g = W.Geometry(ctx, xyz, _carbon(S), store=W.STORE_BF16X2)
+    q, st, status = g.solve_gmres(S.ev([0.5]), [[0, 0, 1.0]], prec=W.PREC_MIXED)
+    assert status == "WFQ_OK" and np.all(q == 0)
+
+
+def test_edge_errors(W, ctx, S):
+    p = _carbon(S)
+    xyz = S.honeycomb_flake(3)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64)
+    with pytest.raises(W.WfqError) as e:
+        g.solve_gmres([0.0], [[1.0, 0, 0]])
+    assert e.value.code == -2                       # omega = 0 (singular)
+    with pytest.raises(W.WfqError) as e:
+        g.solve_gmres([0.02], [[1.0, 0, 0]], prec=W.PREC_MIXED)
+    assert e.value.code == -8                       # mixed needs the bf16 storage
+    dup = np.vstack([xyz, xyz[:1]])
+    with pytest.raises(W.WfqError) as e:
+        W.Geometry(ctx, dup, p)
+    assert e.value.code == -1                       # r_ij = 0
+    bad = xyz.copy()
+    bad[2, 1] = np.nan
+    with pytest.raises(W.WfqError):
+        W.Geometry(ctx, bad, p)
+    with pytest.raises(W.WfqError):
+        W.Geometry(ctx, xyz, dict(p, tau=-1.0))
+    q, st, status = g.solve_gmres([0.02], [[1.0, 0, 0]], max_iter=2, rel_tol=1e-12)
+    assert status == "WFQ_ENOCONV" and st[0]["iters"] == 2
+
+
+def test_edge_dense_kbar_no_cutoff(W, ctx, orc, S):
+    xyz = S.random_cluster(300, seed=44)
+    p = _carbon(S, r0=2.7, cutoff_eps=0.0)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64)
+    assert g.info()["nnz"] == 300 * 299
+    sysm = orc.System(xyz, p)
+    om = S.ev(0.8)
+    x = S.random_complex((300, 1), seed=1)
+    y = np.empty_like(x)
+    g.apply([om], x, y)
+    ref = _oracle_apply(orc, sysm, sysm.z(om), x[:, 0])
+    assert np.abs(y[:, 0] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------------------- full size
+
+@pytest.mark.slow
+def test_cnt20k_full_size_mixed_block_gmres(W, ctx, orc, S):
+    """The cnt20k workload as the bench runs it (64 frequencies x 3 directions, mixed
+    GMRES(50) with FP64 refinement): every column's FP64 residual <= 1e-8; sampled
+    columns re-checked by the oracle's own operator (on-the-fly D, its own CSR)."""
+    wl = S.workload("cnt20k")
+    xyz, p = wl["xyz"], wl["params"]
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 | W.STORE_BF16X2)
+    q, st, status = g.solve_gmres(wl["omega"], wl["dirs"], m=50, rel_tol=1e-8, max_iter=3000,
+                                  prec=W.PREC_MIXED)
+    assert status == "WFQ_OK"
+    assert max(s["rel_residual"] for s in st) <= 1e-8
+    csr = _oracle_csr(orc, xyz, p)
+    op = orc.Operator.on_the_fly(xyz, p["eta"], csr)
+    rng = np.random.default_rng(7)
+    for c in rng.choice(q.shape[1], size=3, replace=False):
+        f, d = divmod(int(c), 3)
+        R = orc.rhs_csr(xyz, csr, wl["dirs"][d]).astype(complex)
+        rr = op.residual_norm(orc.z_of_omega(wl["omega"][f], p), R, q[:, c]) / np.linalg.norm(R)
+        assert rr <= 1.2e-8, (c, rr)
+        assert abs(q[:, c].sum()) <= 1e-9 * np.abs(q[:, c]).sum()
