@@ -163,6 +163,31 @@ int wfq_geometry_info(const wfq_geom *g, int64_t *n, int64_t *nnz, int64_t *devi
 int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, void *y,
               int prec, void *stream);
 
+/* Allocation-free variant of wfq_apply with WFQ_PREC_MIXED (the paper has no
+ * counterpart: this is a deployment facility).  It is for callers that must not
+ * allocate device memory during the apply -- code that runs inside a fixed memory
+ * budget or arena, or in a context where cudaMalloc is not allowed or would stall the
+ * device -- and it computes exactly what wfq_apply(..., WFQ_PREC_MIXED, ...) computes
+ * with the same kernels.
+ *   - x, y: DEVICE pointers, N x ncplx complex64 atom-major (host pointers are
+ *     rejected with WFQ_EINVAL, since staging them would allocate).  omega: host,
+ *     ncplx values.  The caller still owns and passes all inputs and outputs.
+ *   - Scratch (the bf16 planes of x, u = D x and the shifts) lives in one static
+ *     32 MiB device array that every device which loads the library keeps until the
+ *     process exits.  A call needing more -- about 4*ceil64(2*ncplx)*ceil128(N) +
+ *     8*N*ncplx bytes -- fails with WFQ_EINVAL and a message; use wfq_apply then.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the one array and every call overwrites what it reads, so no
+ *     clearing is needed; calls whose work overlaps on the GPU (different streams,
+ *     threads or devices' streams without ordering) race on it and must be
+ *     serialised by the caller.
+ *   - Needs WFQ_STORE_BF16X2 (else WFQ_EUNSUPPORTED).  No device memory is allocated
+ *     or freed by this call. */
+int wfq_apply_mixed_noalloc(wfq_geom *g, int64_t ncplx, const double *omega, const void *x,
+                            void *y, void *stream);
+
 /* Right-hand sides R (Eq. 13 with the potential of Eq. 2) for ndir field
  * directions.  dirs: host, ndir x 3 (need not be unit vectors; the field is E0 * dir).
  * R: N x ndir atom-major real (FP64). */

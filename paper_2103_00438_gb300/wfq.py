@@ -22,7 +22,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 # every symbol include/wfq.h declares
 EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry", "wfq_free_geometry",
            "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_qmr",
-           "wfq_polarizability", "wfq_profile", "wfq_profile_read"]
+           "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc"]
 KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE = 0, 1, 2
 
 
@@ -71,6 +71,7 @@ def load(path: str | None = None):
     L.wfq_solve_gmres.argtypes = [_P, I64, _P, INT, _P, D, INT, D, INT, INT, _P, _P, _P]
     L.wfq_solve_qmr.argtypes = [_P, I64, _P, INT, _P, D, D, INT, INT, INT, _P, _P, _P]
     L.wfq_polarizability.argtypes = [_P, I64, _P, D, _P, _P]
+    L.wfq_apply_mixed_noalloc.argtypes = [_P, I64, _P, _P, _P, _P]
     L.wfq_profile.argtypes = [_P, INT]
     L.wfq_profile_read.argtypes = [_P, INT, ctypes.POINTER(I64), ctypes.POINTER(D)]
     for name in EXPORTS:
@@ -183,6 +184,13 @@ class Geometry:
         """y = (A - z(omega_c) I) x; x, y: (n, ncplx) complex128 (FP64) / complex64 (MIXED)."""
         om = _host_f64(np.atleast_1d(omega))
         _check(_lib.wfq_apply(self.h, len(om), _ptr(om), _ptr(x), _ptr(y), int(prec), _stream_handle(stream)))
+        return y
+
+    def apply_mixed_noalloc(self, omega, x, y, stream=None):
+        """wfq_apply_mixed_noalloc: the mixed apply with the library's static scratch
+        array instead of any allocation; x, y must be device (torch CUDA) complex64."""
+        om = _host_f64(np.atleast_1d(omega))
+        _check(_lib.wfq_apply_mixed_noalloc(self.h, len(om), _ptr(om), _ptr(x), _ptr(y), _stream_handle(stream)))
         return y
 
     def rhs(self, dirs, E0=1.0, out=None, stream=None):
