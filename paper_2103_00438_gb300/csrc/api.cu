@@ -100,6 +100,17 @@ KScope::~KScope() {
     ctx->timer.pending[kind].emplace_back(e0, e1);
 }
 
+int check_device_error(wfq_ctx *ctx, cudaStream_t s) {
+    int h = 0;
+    WFQ_CUDA(cudaMemcpyAsync(&h, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    WFQ_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) {
+        cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), s);
+        return fail(WFQ_ETIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(h) + ")");
+    }
+    return WFQ_OK;
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -226,6 +237,13 @@ int wfq_create(wfq_ctx **out, int device) {
     }
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    e = cudaMalloc(&ctx->dev_err, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->dev_err, 0, 256);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(ctx->pool);
+        delete ctx;
+        return fail(WFQ_ECUDA, std::string("context flag allocation: ") + cudaGetErrorString(e));
+    }
     *out = ctx;
     return WFQ_OK;
 }
@@ -234,6 +252,7 @@ int wfq_destroy(wfq_ctx *ctx) {
     if (!ctx) return WFQ_OK;
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
+    if (ctx->dev_err) cudaFree(ctx->dev_err);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     delete ctx;
     return WFQ_OK;

@@ -82,6 +82,7 @@ struct wfq_ctx {
     int device = 0;
     int num_sms = 0;
     cudaMemPool_t pool = nullptr;
+    int *dev_err = nullptr;   // device flag: non-zero after a bounded wait in a kernel gave up
     wfq::KernelTimer timer;
 };
 
@@ -148,6 +149,9 @@ struct KScope {
     KScope(wfq_ctx *c, int k, cudaStream_t st);
     ~KScope();
 };
+
+// WFQ_ETIMEOUT (and clears the flag) if a kernel reported a bounded wait that gave up.
+int check_device_error(wfq_ctx *ctx, cudaStream_t s);
 
 // True if p is a device (or managed) pointer usable by kernels.
 bool is_device_ptr(const void *p);

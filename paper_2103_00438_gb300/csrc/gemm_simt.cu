@@ -67,9 +67,4 @@ int gemm_3xbf16_simt(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi, 
     return WFQ_OK;
 }
 
-int gemm_3xbf16(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi, const __nv_bfloat16 *Xlo, float *U,
-                int64_t ldu, cudaStream_t s) {
-    return gemm_3xbf16_simt(g, cpad, Xhi, Xlo, U, ldu, s);
-}
-
 }  // namespace wfq

@@ -1,0 +1,23 @@
+// libwfq entry to the tcgen05 GEMM of gemm_tc.cuh (the dense product of the mixed
+// operator, U = D X with three bf16 products).
+#include "common.h"
+#include "gemm_tc.cuh"
+
+namespace wfq {
+
+int gemm_3xbf16(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi, const __nv_bfloat16 *Xlo, float *U,
+                int64_t ldu, cudaStream_t s) {
+    std::string msg;
+    int launches = 0;
+    KScope ks(g->ctx, WFQ_KT_GEMM_MIXED, s);
+    cudaError_t e = tc::gemm3_tc(g->Dhi, g->Dlo, g->n, g->npad, Xhi, Xlo, cpad, U, ldu, g->ctx->num_sms,
+                                 g->ctx->dev_err, s, &launches, &msg);
+    for (int i = 0; i < launches; ++i) note_launch();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(WFQ_ECUDA, "tensor-core GEMM: " + (msg.empty() ? std::string(cudaGetErrorString(e)) : msg));
+    }
+    return WFQ_OK;
+}
+
+}  // namespace wfq

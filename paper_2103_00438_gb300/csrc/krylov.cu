@@ -383,6 +383,7 @@ struct Common {
 
 static int fill_stats(const SolveArgs &a, Common &cm, const std::vector<int> &iters, int cycles, int status,
                       bool breakdown_any, const std::vector<int> &breakdown) {
+    WFQ_TRY(check_device_error(cm.g->ctx, cm.s));
     std::vector<double2> rn(cm.cc), bn(cm.cc);
     WFQ_CUDA(cudaMemcpyAsync(rn.data(), cm.rnorm.ptr, sizeof(double2) * cm.cc, cudaMemcpyDeviceToHost, cm.s));
     WFQ_CUDA(cudaMemcpyAsync(bn.data(), cm.bnorm.ptr, sizeof(double2) * cm.cc, cudaMemcpyDeviceToHost, cm.s));
@@ -461,7 +462,7 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
                                                  cm.converged.ptr); note_launch();
         WFQ_CUDA(cudaGetLastError());
         WFQ_CUDA(cudaMemcpyAsync(conv_h.data(), cm.converged.ptr, sizeof(int) * cc, cudaMemcpyDeviceToHost, s));
-        WFQ_CUDA(cudaStreamSynchronize(s));
+        WFQ_TRY(check_device_error(g->ctx, s));
         bool all_conv = std::all_of(conv_h.begin(), conv_h.end(), [](int v) { return v != 0; });
         if (all_conv || total >= a.max_iter) break;
 
@@ -734,7 +735,7 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         WFQ_CUDA(cudaGetLastError());
         WFQ_CUDA(cudaMemcpyAsync(conv_h.data(), cm.converged.ptr, sizeof(int) * cc, cudaMemcpyDeviceToHost, s));
         WFQ_CUDA(cudaMemcpyAsync(brk_h.data(), brk.ptr, sizeof(int) * cc, cudaMemcpyDeviceToHost, s));
-        WFQ_CUDA(cudaStreamSynchronize(s));
+        WFQ_TRY(check_device_error(g->ctx, s));
         bool unfinished = false;
         for (int64_t c = 0; c < cc; ++c)
             if (!conv_h[c] && !brk_h[c]) unfinished = true;
