@@ -83,9 +83,13 @@ typedef struct {
 /* Arithmetic of an apply / of the inner Krylov iterations. */
 enum {
     WFQ_PREC_FP64 = 0,     /* FP64 operator, complex128 vectors */
-    WFQ_PREC_MIXED = 1     /* D.x from 3 bf16 products (hi.hi + hi.lo + lo.hi) with FP32
-                              accumulation, complex64 vectors; solves add FP64 iterative
-                              refinement on top */
+    WFQ_PREC_MIXED = 1,    /* D.x from 3 bf16 products (hi.hi + hi.lo + lo.hi) with FP32
+                              accumulation, complex64 vectors; solves add iterative
+                              refinement on top, whose true residual uses WFQ_PREC_DF */
+    WFQ_PREC_DF = 2        /* wfq_apply only: complex128 vectors, D.x with FP64 operands split
+                              into float pairs and double-float accumulation (~2^-48 relative
+                              per product) on the FP32 pipes; needs WFQ_STORE_FP64 and more
+                              than 4 columns, else identical to WFQ_PREC_FP64 */
 };
 
 /* Per-solve statistics. */
@@ -121,14 +125,20 @@ enum {
     WFQ_KT_GEMM_MIXED = 0,   /* 3xBF16 tensor-core GEMM  U = D X   (mixed apply) */
     WFQ_KT_DAPPLY_FP64 = 1,  /* FP64 dense product U = D X (stored or recomputed D) */
     WFQ_KT_SPARSE = 2,       /* sparse term and shift  Y = Kbar U - P U - z X */
-    WFQ_KT_COUNT = 3
+    WFQ_KT_ORTHO = 3,        /* Arnoldi orthogonalisation of one GMRES step (projections,
+                                norm, Givens, scaling) / the vector updates of a QMR step */
+    WFQ_KT_RESIDUAL = 4,     /* FP64 true residual of a cycle (gathers, product, norms) */
+    WFQ_KT_COUNT = 5
 };
 
 /* enable != 0: reset the counters and start recording; enable == 0: stop. */
 int wfq_profile(wfq_ctx *ctx, int enable);
 
-/* Launches and summed device milliseconds of kernel class `kind` (WFQ_KT_*). */
-int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms);
+/* Launches, summed device milliseconds and summed work of kernel class `kind` (WFQ_KT_*).
+ * Work: WFQ_KT_GEMM_MIXED -- tensor flops of the three bf16 products, 6 N^2 C per launch
+ * (C = real columns of that launch); WFQ_KT_DAPPLY_FP64 -- 2 N^2 C flops; other classes 0.
+ * Any out-pointer may be NULL. */
+int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms, double *work);
 
 /* ---------------------------------------------------------------- geometry */
 
@@ -156,7 +166,7 @@ int wfq_geometry_info(const wfq_geom *g, int64_t *n, int64_t *nnz, int64_t *devi
  * through the factored form of Eq. 17):  u = D x,  y = Kbar u - P u - z x.
  * omega: host array of ncplx frequencies (hartree), one per column; omega_c = 0 is
  * allowed here (z = 0).  x, y: N x ncplx atom-major blocks, complex128 for
- * WFQ_PREC_FP64 and complex64 for WFQ_PREC_MIXED; x and y must not overlap.
+ * WFQ_PREC_FP64 / WFQ_PREC_DF and complex64 for WFQ_PREC_MIXED; x and y must not overlap.
  * FP64 uses the stored FP64 D if present, else recomputes D (matrix-free).
  * MIXED needs WFQ_STORE_BF16X2 (else WFQ_EUNSUPPORTED).  Asynchronous on `stream`
  * when x and y are device pointers. */

@@ -51,12 +51,14 @@ cudaEvent_t KernelTimer::get() {
 
 void KernelTimer::collect() {
     for (int k = 0; k < WFQ_KT_COUNT; ++k) {
-        for (auto &pr : pending[k]) {
+        for (size_t q = 0; q < pending[k].size(); ++q) {
+            auto &pr = pending[k][q];
             float t = 0.f;
             if (cudaEventSynchronize(pr.second) == cudaSuccess &&
                 cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) {
                 ms[k] += t;
                 launches[k] += 1;
+                work[k] += pending_work[k][q];
             } else {
                 cudaGetLastError();
             }
@@ -64,6 +66,7 @@ void KernelTimer::collect() {
             pool.push_back(pr.second);
         }
         pending[k].clear();
+        pending_work[k].clear();
     }
 }
 
@@ -72,6 +75,7 @@ void KernelTimer::reset() {
     for (int k = 0; k < WFQ_KT_COUNT; ++k) {
         launches[k] = 0;
         ms[k] = 0.0;
+        work[k] = 0.0;
     }
 }
 
@@ -81,7 +85,7 @@ KernelTimer::~KernelTimer() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
-KScope::KScope(wfq_ctx *c, int k, cudaStream_t st) : ctx(c), kind(k), s(st) {
+KScope::KScope(wfq_ctx *c, int k, cudaStream_t st, double w) : ctx(c), kind(k), s(st), work(w) {
     if (!ctx->timer.enabled) return;
     std::lock_guard<std::mutex> lk(ctx->timer.mu);
     e0 = ctx->timer.get();
@@ -98,6 +102,7 @@ KScope::~KScope() {
     }
     cudaEventRecord(e1, s);
     ctx->timer.pending[kind].emplace_back(e0, e1);
+    ctx->timer.pending_work[kind].push_back(work);
 }
 
 int check_device_error(wfq_ctx *ctx, cudaStream_t s) {
@@ -267,7 +272,7 @@ int wfq_profile(wfq_ctx *ctx, int enable) {
     return WFQ_OK;
 }
 
-int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms) {
+int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms, double *work) {
     if (!ctx) return fail(WFQ_EINVAL, "NULL context");
     if (kind < 0 || kind >= WFQ_KT_COUNT) return fail(WFQ_EINVAL, "unknown kernel class");
     DeviceGuard dg(ctx->device);
@@ -275,6 +280,7 @@ int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms
     ctx->timer.collect();
     if (launches) *launches = ctx->timer.launches[kind];
     if (total_ms) *total_ms = ctx->timer.ms[kind];
+    if (work) *work = ctx->timer.work[kind];
     return WFQ_OK;
 }
 
@@ -379,7 +385,8 @@ int wfq_geometry_info(const wfq_geom *g, int64_t *n, int64_t *nnz, int64_t *devi
 int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, void *y, int prec, void *stream) {
     if (!g || !omega || !x || !y) return fail(WFQ_EINVAL, "NULL argument");
     if (ncplx < 1) return fail(WFQ_EINVAL, "ncplx must be >= 1");
-    if (prec != WFQ_PREC_FP64 && prec != WFQ_PREC_MIXED) return fail(WFQ_EINVAL, "unknown precision");
+    if (prec != WFQ_PREC_FP64 && prec != WFQ_PREC_MIXED && prec != WFQ_PREC_DF)
+        return fail(WFQ_EINVAL, "unknown precision");
     if (!finite_all(omega, ncplx)) return fail(WFQ_EINVAL, "omega has a non-finite entry");
     if (prec == WFQ_PREC_MIXED && !g->Dhi) return fail(WFQ_EUNSUPPORTED, "mixed apply needs WFQ_STORE_BF16X2");
     DeviceGuard dg(g->ctx->device);
@@ -390,13 +397,16 @@ int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, vo
     DevBuf<double2> z;
     WFQ_TRY(z.alloc(g->ctx, ncplx, s));
     WFQ_CUDA(cudaMemcpyAsync(z.ptr, zh.data(), sizeof(double2) * ncplx, cudaMemcpyHostToDevice, s));
-    if (prec == WFQ_PREC_FP64) {
+    if (prec == WFQ_PREC_FP64 || prec == WFQ_PREC_DF) {
         Staged<double2> X, Y;
         WFQ_TRY(X.in(g->ctx, static_cast<const double2 *>(x), nc, true, s));
         WFQ_TRY(Y.in(g->ctx, static_cast<double2 *>(y), nc, false, s));
         DevBuf<double2> U;
         WFQ_TRY(U.alloc(g->ctx, nc, s));
-        WFQ_TRY(d_apply_fp64(g, ncplx, X.dev, U.ptr, s));
+        if (prec == WFQ_PREC_DF)
+            WFQ_TRY(d_apply_df(g, ncplx, X.dev, U.ptr, s));
+        else
+            WFQ_TRY(d_apply_fp64(g, ncplx, X.dev, U.ptr, s));
         WFQ_TRY(sparse_shift_fp64(g, ncplx, U.ptr, X.dev, z.ptr, Y.dev, s));
         WFQ_TRY(Y.out(s));
     } else {

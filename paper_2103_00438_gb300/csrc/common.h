@@ -68,8 +68,10 @@ struct KernelTimer {
     bool enabled = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[WFQ_KT_COUNT];
     std::vector<cudaEvent_t> pool;
+    std::vector<double> pending_work[WFQ_KT_COUNT];
     int64_t launches[WFQ_KT_COUNT] = {};
     double ms[WFQ_KT_COUNT] = {};
+    double work[WFQ_KT_COUNT] = {};
     cudaEvent_t get();
     void collect();
     void reset();
@@ -145,8 +147,9 @@ struct KScope {
     wfq_ctx *ctx;
     int kind;
     cudaStream_t s;
+    double work;
     cudaEvent_t e0 = nullptr;
-    KScope(wfq_ctx *c, int k, cudaStream_t st);
+    KScope(wfq_ctx *c, int k, cudaStream_t st, double w = 0.0);
     ~KScope();
 };
 
@@ -172,6 +175,11 @@ int launch_polarizability(const wfq_geom *g, int64_t ncols, const double2 *q, do
 
 // U = D X in FP64 (stored FP64 D if present, else recomputed from the coordinates).
 int d_apply_fp64(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s);
+
+// U = D X with double-float products (FP64 operands split into float pairs, about 48
+// significant bits) when the FP64 D is stored and there are more than 4 columns; else
+// the FP64 kernels.  Used for the refinement residual of mixed-precision solves.
+int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s);
 
 // U = D X with 3 bf16 products and FP32 accumulation (stored bf16 planes).
 // scratch: at least mixed_scratch_bytes(g, cc) bytes of device memory.

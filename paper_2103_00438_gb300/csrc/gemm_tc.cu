@@ -9,7 +9,7 @@ int gemm_3xbf16(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi, const
                 int64_t ldu, cudaStream_t s) {
     std::string msg;
     int launches = 0;
-    KScope ks(g->ctx, WFQ_KT_GEMM_MIXED, s);
+    KScope ks(g->ctx, WFQ_KT_GEMM_MIXED, s, 6.0 * (double)g->n * (double)g->n * (double)ldu);
     cudaError_t e = tc::gemm3_tc(g->Dhi, g->Dlo, g->n, g->npad, Xhi, Xlo, cpad, U, ldu, g->ctx->num_sms,
                                  g->ctx->dev_err, s, &launches, &msg);
     for (int i = 0; i < launches; ++i) note_launch();

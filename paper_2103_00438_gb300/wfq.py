@@ -17,13 +17,13 @@ WFQ_OK = 0
 STATUS = {0: "WFQ_OK", -1: "WFQ_EINVAL", -2: "WFQ_ESINGULAR", -3: "WFQ_ENOMEM", -4: "WFQ_ENOCONV",
           -5: "WFQ_EBREAKDOWN", -6: "WFQ_ETIMEOUT", -7: "WFQ_ECUDA", -8: "WFQ_EUNSUPPORTED"}
 STORE_FP64, STORE_BF16X2 = 1, 2
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2
 
 # every symbol include/wfq.h declares
 EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry", "wfq_free_geometry",
            "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_qmr",
            "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc"]
-KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE = 0, 1, 2
+KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE, KT_ORTHO, KT_RESIDUAL = 0, 1, 2, 3, 4
 
 
 class WfqError(RuntimeError):
@@ -73,7 +73,7 @@ def load(path: str | None = None):
     L.wfq_polarizability.argtypes = [_P, I64, _P, D, _P, _P]
     L.wfq_apply_mixed_noalloc.argtypes = [_P, I64, _P, _P, _P, _P]
     L.wfq_profile.argtypes = [_P, INT]
-    L.wfq_profile_read.argtypes = [_P, INT, ctypes.POINTER(I64), ctypes.POINTER(D)]
+    L.wfq_profile_read.argtypes = [_P, INT, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
     for name in EXPORTS:
         if name not in ("wfq_last_error", "wfq_kernel_launches"):
             getattr(L, name).restype = INT
@@ -127,10 +127,10 @@ class Context:
         _check(_lib.wfq_profile(self.h, 1 if enable else 0))
 
     def profile_read(self, kind: int):
-        """(launches, total device ms) of a kernel class since profile(True)."""
-        n, ms = ctypes.c_int64(), ctypes.c_double()
-        _check(_lib.wfq_profile_read(self.h, int(kind), ctypes.byref(n), ctypes.byref(ms)))
-        return n.value, ms.value
+        """(launches, total device ms, total work) of a kernel class since profile(True)."""
+        n, ms, wk = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(_lib.wfq_profile_read(self.h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(wk)))
+        return n.value, ms.value, wk.value
 
     def close(self):
         if self.h:

@@ -115,6 +115,31 @@ def test_apply_mixed_within_derived_bound(W, ctx, orc, S, n, ncplx):
     assert worst <= TAU_MIXED
 
 
+@pytest.mark.parametrize("n,ncplx", [(1000, 3), (1333, 7), (2049, 40)])
+def test_apply_double_float_within_derived_bound(W, ctx, orc, S, n, ncplx):
+    """Double-float D products: operands split into float pairs (48 significant bits),
+    products and sums error-free up to ~2^-48 each, so per element
+        |dy_i| <= TAU_DF * (sum_p Kbar_ip (s_i + s_j) + |z| |x_i|),  s = |D| |x|,
+    with TAU_DF = 8 * 2^-48 * sqrt(N): rounding errors of 2^-48 per step that add up
+    like a random walk over the N-term sum, with a factor 8 of margin."""
+    TAU_DF = 8 * 2.0 ** -48 * np.sqrt(n)
+    xyz = S.random_cluster(n, seed=n + 5)
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64)
+    sysm = orc.System(xyz, p)
+    om = S.ev(np.linspace(0.2, 1.9, ncplx))
+    x = S.random_complex((n, ncplx), seed=11)
+    y = np.empty_like(x)
+    g.apply(om, x, y, prec=W.PREC_DF)
+    worst = 0.0
+    for c in range(ncplx):
+        z = sysm.z(om[c])
+        ref = _oracle_apply(orc, sysm, z, x[:, c])
+        worst = max(worst, float(np.max(np.abs(y[:, c] - ref) / _mixed_bound(sysm, z, x[:, c]))))
+    print("double-float apply: max |dy| / unit bound =", worst)
+    assert worst <= TAU_DF
+
+
 def test_apply_device_pointers_and_stream(W, ctx, orc, S):
     torch = pytest.importorskip("torch")
     n, ncplx = 900, 4
