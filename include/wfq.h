@@ -84,8 +84,10 @@ typedef struct {
 enum {
     WFQ_PREC_FP64 = 0,     /* FP64 operator, complex128 vectors */
     WFQ_PREC_MIXED = 1,    /* D.x from 3 bf16 products (hi.hi + hi.lo + lo.hi) with FP32
-                              accumulation, complex64 vectors; solves add iterative
-                              refinement on top, whose true residual uses WFQ_PREC_DF */
+                              accumulation on the tensor cores, D from the stored bf16 planes
+                              or generated from the coordinates; complex64 vectors; solves
+                              add iterative refinement on top, whose true residual uses
+                              WFQ_PREC_DF (FP64 kernels when D64 is not stored) */
     WFQ_PREC_DF = 2        /* wfq_apply only: complex128 vectors, D.x with FP64 operands split
                               into float pairs and double-float accumulation (~2^-48 relative
                               per product) on the FP32 pipes; needs WFQ_STORE_FP64 and more
@@ -167,9 +169,10 @@ int wfq_geometry_info(const wfq_geom *g, int64_t *n, int64_t *nnz, int64_t *devi
  * omega: host array of ncplx frequencies (hartree), one per column; omega_c = 0 is
  * allowed here (z = 0).  x, y: N x ncplx atom-major blocks, complex128 for
  * WFQ_PREC_FP64 / WFQ_PREC_DF and complex64 for WFQ_PREC_MIXED; x and y must not overlap.
- * FP64 uses the stored FP64 D if present, else recomputes D (matrix-free).
- * MIXED needs WFQ_STORE_BF16X2 (else WFQ_EUNSUPPORTED).  Asynchronous on `stream`
- * when x and y are device pointers. */
+ * FP64 / DF use the stored FP64 D if present, else recompute D (matrix-free).  MIXED uses
+ * the stored bf16 planes if present, else generates the D tiles from the coordinates on
+ * the fly (matrix-free tensor-core path).  Asynchronous on `stream` when x and y are
+ * device pointers. */
 int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, void *y,
               int prec, void *stream);
 

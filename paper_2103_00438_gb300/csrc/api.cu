@@ -388,7 +388,6 @@ int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, vo
     if (prec != WFQ_PREC_FP64 && prec != WFQ_PREC_MIXED && prec != WFQ_PREC_DF)
         return fail(WFQ_EINVAL, "unknown precision");
     if (!finite_all(omega, ncplx)) return fail(WFQ_EINVAL, "omega has a non-finite entry");
-    if (prec == WFQ_PREC_MIXED && !g->Dhi) return fail(WFQ_EUNSUPPORTED, "mixed apply needs WFQ_STORE_BF16X2");
     DeviceGuard dg(g->ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int64_t n = g->n, nc = n * ncplx;
@@ -449,7 +448,6 @@ static int solve_common(bool qmr, wfq_geom *g, int64_t nfreq, const double *omeg
     if (m < 0 || max_iter < 1 || refine_every < 0) return fail(WFQ_EINVAL, "m, max_iter or refine_every out of range");
     if (!(rel_tol > 0.0 && rel_tol < 1.0)) return fail(WFQ_EINVAL, "rel_tol must be in (0, 1)");
     if (prec != WFQ_PREC_FP64 && prec != WFQ_PREC_MIXED) return fail(WFQ_EINVAL, "unknown precision");
-    if (prec == WFQ_PREC_MIXED && !g->Dhi) return fail(WFQ_EUNSUPPORTED, "mixed solve needs WFQ_STORE_BF16X2");
     if (!finite_all(omega, nfreq) || !finite_all(dirs, 3 * (int64_t)ndir) || !std::isfinite(E0) || E0 == 0.0)
         return fail(WFQ_EINVAL, "non-finite omega / direction or E0 = 0");
     for (int64_t f = 0; f < nfreq; ++f)

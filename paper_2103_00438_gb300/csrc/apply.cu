@@ -471,14 +471,14 @@ size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc) {
 
 int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
                   cudaStream_t s) {
-    if (!g->Dhi) return fail(WFQ_EUNSUPPORTED, "mixed apply needs WFQ_STORE_BF16X2");
     const int64_t C = 2 * cc, cpad = mixed_cpad(cc), npad = g->npad;
     __nv_bfloat16 *xhi = reinterpret_cast<__nv_bfloat16 *>(scratch);
     __nv_bfloat16 *xlo = xhi + cpad * npad;
     dim3 grid((unsigned)(npad / 32), (unsigned)((cpad + 31) / 32));
     k_split_bf16<<<grid, 256, 0, s>>>(g->n, npad, C, cpad, reinterpret_cast<const float *>(X), xhi, xlo); note_launch();
     WFQ_CUDA(cudaGetLastError());
-    return gemm_3xbf16(g, cpad, xhi, xlo, reinterpret_cast<float *>(U), C, s);
+    if (g->Dhi) return gemm_3xbf16(g, cpad, xhi, xlo, reinterpret_cast<float *>(U), C, s);
+    return gemm_3xbf16_mf(g, cpad, xhi, xlo, reinterpret_cast<float *>(U), C, s);
 }
 
 }  // namespace wfq

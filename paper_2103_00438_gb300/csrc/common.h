@@ -181,7 +181,8 @@ int d_apply_fp64(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cu
 // the FP64 kernels.  Used for the refinement residual of mixed-precision solves.
 int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s);
 
-// U = D X with 3 bf16 products and FP32 accumulation (stored bf16 planes).
+// U = D X with 3 bf16 products and FP32 accumulation: stored bf16 planes when present,
+// else tiles generated from the coordinates (matrix-free).
 // scratch: at least mixed_scratch_bytes(g, cc) bytes of device memory.
 size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc);
 int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
@@ -198,6 +199,10 @@ int sparse_shift_fp32(const wfq_geom *g, int64_t cc, const float2 *U, const floa
 // columns < ldu of U are written.
 int gemm_3xbf16(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi,
                 const __nv_bfloat16 *Xlo, float *U, int64_t ldu, cudaStream_t s);
+
+// As gemm_3xbf16 with the D tiles generated from the atom records (matrix-free).
+int gemm_3xbf16_mf(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi,
+                   const __nv_bfloat16 *Xlo, float *U, int64_t ldu, cudaStream_t s);
 
 // ------------------------------------------------------------------ solvers
 

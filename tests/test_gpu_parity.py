@@ -140,6 +140,44 @@ def test_apply_double_float_within_derived_bound(W, ctx, orc, S, n, ncplx):
     assert worst <= TAU_DF
 
 
+@pytest.mark.parametrize("n,ncplx", [(1000, 1), (1337, 3), (2049, 8), (129, 2), (3000, 40)])
+def test_apply_mixed_matrix_free_within_derived_bound(W, ctx, orc, S, n, ncplx):
+    """Matrix-free tensor-core path: D tiles generated in FP32 from the coordinates and
+    split into bf16 hi + lo in shared memory; same bound as the stored mixed path."""
+    xyz = S.random_cluster(n, seed=n + 2)
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=0)
+    sysm = orc.System(xyz, p)
+    om = S.ev(np.linspace(0.3, 1.5, ncplx))
+    x = S.random_complex((n, ncplx), seed=19).astype(np.complex64)
+    y = np.empty_like(x)
+    g.apply(om, x, y, prec=W.PREC_MIXED)
+    worst = 0.0
+    for c in range(ncplx):
+        z = sysm.z(om[c])
+        xc = x[:, c].astype(np.complex128)
+        ref = _oracle_apply(orc, sysm, z, xc)
+        worst = max(worst, float(np.max(np.abs(y[:, c] - ref) / _mixed_bound(sysm, z, xc))))
+    print("matrix-free mixed apply: max |dy| / unit bound =", worst)
+    assert worst <= TAU_MIXED
+
+
+def test_matrix_free_equals_stored_mixed(W, ctx, S):
+    """The generated tiles are the stored bf16 planes up to FP32 rounding of D: the two
+    mixed applies agree far inside the mixed tolerance."""
+    n = 2500
+    xyz = S.random_cluster(n, seed=77)
+    p = _carbon(S, r0=2.7)
+    gs = W.Geometry(ctx, xyz, p, store=W.STORE_BF16X2)
+    gm = W.Geometry(ctx, xyz, p, store=0)
+    om = S.ev([0.4, 1.1])
+    x = S.random_complex((n, 2), seed=4).astype(np.complex64)
+    ys, ym = np.empty_like(x), np.empty_like(x)
+    gs.apply(om, x, ys, prec=W.PREC_MIXED)
+    gm.apply(om, x, ym, prec=W.PREC_MIXED)
+    assert np.abs(ys - ym).max() <= 1e-4 * np.abs(ys).max()
+
+
 def test_apply_device_pointers_and_stream(W, ctx, orc, S):
     torch = pytest.importorskip("torch")
     n, ncplx = 900, 4
@@ -197,6 +235,18 @@ def test_gmres_mixed_flake1k_acceptance(W, ctx, orc, flake, m):
     rr = sysm.operator().residual_norm(z, R, q[:, 0]) / np.linalg.norm(R)
     assert rr <= 1e-8 and abs(rr - st[0]["rel_residual"]) <= 1e-10
     print("mixed GMRES stats", st[0])
+
+
+def test_gmres_mixed_matrix_free_flake1k_acceptance(W, ctx, orc, flake):
+    """No D stored at all: matrix-free tensor-core inner products, FP64 recomputed
+    residual; same acceptance bar."""
+    wl, sysm, om, q_lu = flake
+    g = W.Geometry(ctx, wl["xyz"], wl["params"], store=0)
+    q, st, status = g.solve_gmres([om], [[1.0, 0, 0]], m=30, rel_tol=1e-8, max_iter=2000, prec=W.PREC_MIXED)
+    assert status == "WFQ_OK", st
+    a = g.polarizability(q)[0, 0]
+    a_ref = orc.alpha(wl["xyz"], q_lu)[0]
+    assert abs(a - a_ref) <= 1e-6 * abs(a_ref)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -298,8 +348,8 @@ def test_edge_errors(W, ctx, S):
         g.solve_gmres([0.0], [[1.0, 0, 0]])
     assert e.value.code == -2                       # omega = 0 (singular)
     with pytest.raises(W.WfqError) as e:
-        g.solve_gmres([0.02], [[1.0, 0, 0]], prec=W.PREC_MIXED)
-    assert e.value.code == -8                       # mixed needs the bf16 storage
+        g.solve_gmres([0.02], [[1.0, 0, 0]], prec=7)
+    assert e.value.code == -1                       # unknown precision
     dup = np.vstack([xyz, xyz[:1]])
     with pytest.raises(W.WfqError) as e:
         W.Geometry(ctx, dup, p)
