@@ -141,7 +141,7 @@ static int galloc(wfq_geom *g, T **p, size_t count) {
 }
 
 static void free_geom(wfq_geom *g) {
-    void *ptrs[] = {g->xyz, g->atom64, g->atom32, g->eta, g->rowptr, g->col,
+    void *ptrs[] = {g->xyz, g->atom64, g->atom32, g->atomdf, g->eta, g->rowptr, g->col,
                     g->val64, g->val32, g->D64, g->Dhi, g->Dlo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -329,11 +329,25 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
         a32[i] = make_float4((float)xyz[3 * i], (float)xyz[3 * i + 1], (float)xyz[3 * i + 2], (float)w);
     }
     for (int64_t i = n; i < g->npad; ++i) a32[i] = make_float4(1e30f, 1e30f, 1e30f, 1.0f);
+    std::vector<float4> adf(2 * n);
+    auto split = [](double v, float &h, float &l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+    };
+    for (int64_t i = 0; i < n; ++i) {
+        float xh, xl, yh, yl, zh, zl;
+        split(xyz[3 * i], xh, xl);
+        split(xyz[3 * i + 1], yh, yl);
+        split(xyz[3 * i + 2], zh, zl);
+        adf[2 * i] = make_float4(xh, xl, yh, yl);
+        adf[2 * i + 1] = make_float4(zh, zl, (float)(wfac / eta_h[i]), 0.0f);
+    }
     std::vector<float> val32(val.begin(), val.end());
 
     if ((rc = galloc(g, &g->xyz, 3 * n))) return bail(rc);
     if ((rc = galloc(g, &g->atom64, n))) return bail(rc);
     if ((rc = galloc(g, &g->atom32, g->npad))) return bail(rc);
+    if ((rc = galloc(g, &g->atomdf, 2 * n))) return bail(rc);
     if ((rc = galloc(g, &g->eta, n))) return bail(rc);
     if ((rc = galloc(g, &g->rowptr, n + 1))) return bail(rc);
     if ((rc = galloc(g, &g->col, g->nnz))) return bail(rc);
@@ -354,6 +368,7 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     if ((rc = up(g->xyz, xyz, sizeof(double) * 3 * n))) return bail(rc);
     if ((rc = up(g->atom64, a64.data(), sizeof(atom64_t) * n))) return bail(rc);
     if ((rc = up(g->atom32, a32.data(), sizeof(float4) * g->npad))) return bail(rc);
+    if ((rc = up(g->atomdf, adf.data(), sizeof(float4) * 2 * n))) return bail(rc);
     if ((rc = up(g->eta, eta_h.data(), sizeof(double) * n))) return bail(rc);
     if ((rc = up(g->rowptr, rowptr.data(), sizeof(int64_t) * (n + 1)))) return bail(rc);
     if ((rc = up(g->col, col.data(), sizeof(int32_t) * g->nnz))) return bail(rc);

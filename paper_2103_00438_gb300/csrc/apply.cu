@@ -263,8 +263,149 @@ __global__ void __launch_bounds__(256) k_dgemm_df(int64_t n, int64_t C, const do
     }
 }
 
+// ------------------------------------------------------------------ double-float matrix-free D
+
+// Exact a - b of two floats as an unevaluated sum (Knuth's two-difference).
+__device__ __forceinline__ void two_diff(float a, float b, float &s, float &e) {
+    s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb));
+}
+
+// (ah + al) - (bh + bl) as a normalised float pair.
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float &h, float &l) {
+    float s, e;
+    two_diff(ah, bh, s, e);
+    e = __fadd_rn(e, __fsub_rn(al, bl));
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+
+// (h + l)^2 accumulated into (sh, sl) with a two-sum.
+__device__ __forceinline__ void df_sqr_acc(float h, float l, float &sh, float &sl) {
+    const float p = __fmul_rn(h, h);
+    const float e = fmaf(h, h, -p) + 2.0f * h * l;
+    const float s = __fadd_rn(sh, p);
+    const float v = __fsub_rn(s, sh);
+    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(p, v));
+    sh = s;
+    sl = sl + t + e;
+}
+
+// D_ik of Eq. 3 as a float pair.  Far pairs (r >= 6 sigma, where erf rounds to 1 in FP64):
+// 1/r from the float-pair coordinates -- r^2 in double-float, FP32 rsqrt refined by one
+// Newton step in double-float (relative error ~1e-13).  Near pairs and the diagonal: FP64.
+__device__ __forceinline__ void d_pair_df(const float4 *__restrict__ adf, const atom64_t *__restrict__ a64,
+                                          const double *__restrict__ eta, int64_t i, int64_t k, float &dh,
+                                          float &dl) {
+    if (i == k) {
+        df_split(eta[i], dh, dl);
+        return;
+    }
+    const float4 pi0 = adf[2 * i], pi1 = adf[2 * i + 1];   // (xh, xl, yh, yl), (zh, zl, w, -)
+    const float4 pk0 = adf[2 * k], pk1 = adf[2 * k + 1];
+    float xh, xl, yh, yl, zh, zl;
+    df_sub(pi0.x, pi0.y, pk0.x, pk0.y, xh, xl);
+    df_sub(pi0.z, pi0.w, pk0.z, pk0.w, yh, yl);
+    df_sub(pi1.x, pi1.y, pk1.x, pk1.y, zh, zl);
+    float rh = 0.f, rl = 0.f;
+    df_sqr_acc(xh, xl, rh, rl);
+    df_sqr_acc(yh, yl, rh, rl);
+    df_sqr_acc(zh, zl, rh, rl);
+    const float s2 = pi1.z * pi1.z + pk1.z * pk1.z;
+    if (rh < 36.5f * s2) {   // near pair: FP64 (erf matters)
+        df_split(d_pair64(a64[i], a64[k]), dh, dl);
+        return;
+    }
+    const float y0 = rsqrtf(rh);
+    const float th = __fmul_rn(y0, y0);
+    const float tl = fmaf(y0, y0, -th);
+    const float uh = __fmul_rn(rh, th);
+    const float ul = fmaf(rh, th, -uh) + rh * tl + rl * th;
+    const float delta = __fsub_rn(1.0f, uh) - ul;   // 1 - r^2 y0^2, ~1e-7
+    dh = y0;
+    dl = 0.5f * y0 * delta;
+}
+
+// As k_dgemm_df with the D tile generated per use (matrix-free); TN columns per thread.
+template <int TN>
+__global__ void __launch_bounds__(256) k_dotf_df(int64_t n, int64_t C, const float4 *__restrict__ adf,
+                                                 const atom64_t *__restrict__ a64, const double *__restrict__ eta,
+                                                 const double *__restrict__ X, double *__restrict__ U) {
+    constexpr int BN = 16 * TN;
+    __shared__ float Ah[16][64], Al[16][64], Bh[16][BN], Bl[16][BN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * BN;
+    float sh[4][TN] = {}, sl[4][TN] = {};
+    for (int64_t k0 = 0; k0 < n; k0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = tid + l * 256;
+            const int r = e & 63, kk = e >> 6;
+            const int64_t gi = m0 + r, gk = k0 + kk;
+            float h = 0.f, lo = 0.f;
+            if (gi < n && gk < n) d_pair_df(adf, a64, eta, gi, gk, h, lo);
+            Ah[kk][r] = h;
+            Al[kk][r] = lo;
+        }
+        for (int e = tid; e < 16 * BN; e += 256) {
+            const int kb = e / BN, cb = e % BN;
+            const int64_t bk = k0 + kb, bc = n0 + cb;
+            df_split((bk < n && bc < C) ? X[bk * C + bc] : 0.0, Bh[kb][cb], Bl[kb][cb]);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            float ah[4], al[4], bh[TN], bl[TN];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                ah[t] = Ah[kk][ty * 4 + t];
+                al[t] = Al[kk][ty * 4 + t];
+            }
+#pragma unroll
+            for (int t = 0; t < TN; ++t) {
+                bh[t] = Bh[kk][tx * TN + t];
+                bl[t] = Bl[kk][tx * TN + t];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) df_mac(ah[r], al[r], bh[c], bl[c], sh[r][c], sl[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t gi = m0 + ty * 4 + r;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int64_t gc = n0 + tx * TN + c;
+            if (gc < C) U[gi * C + gc] = (double)sh[r][c] + (double)sl[r][c];
+        }
+    }
+}
+
 int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
-    if (!g->D64) return d_apply_fp64(g, cc, X, U, s);
+    if (!g->D64) {
+        // matrix-free double-float product
+        const int64_t n = g->n, C = 2 * cc;
+        if (C <= 2) return d_apply_fp64(g, cc, X, U, s);
+        KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);
+        const double *x = reinterpret_cast<const double *>(X);
+        double *u = reinterpret_cast<double *>(U);
+        if (C <= 32) {
+            dim3 grid((unsigned)((C + 31) / 32), (unsigned)((n + 63) / 64));
+            if (grid.y > 65535u) return fail(WFQ_EUNSUPPORTED, "double-float apply: too many rows");
+            k_dotf_df<2><<<grid, 256, 0, s>>>(n, C, g->atomdf, g->atom64, g->eta, x, u); note_launch();
+        } else {
+            dim3 grid((unsigned)((C + 63) / 64), (unsigned)((n + 63) / 64));
+            if (grid.y > 65535u) return fail(WFQ_EUNSUPPORTED, "double-float apply: too many rows");
+            k_dotf_df<4><<<grid, 256, 0, s>>>(n, C, g->atomdf, g->atom64, g->eta, x, u); note_launch();
+        }
+        WFQ_CUDA(cudaGetLastError());
+        return WFQ_OK;
+    }
     const int64_t n = g->n, C = 2 * cc;
     if (C <= 8) return d_apply_fp64(g, cc, X, U, s);   // few columns: memory bound, FP64 GEMV
     KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);

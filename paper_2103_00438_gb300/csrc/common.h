@@ -101,6 +101,7 @@ struct wfq_geom {
     double *xyz = nullptr;      // n x 3
     wfq::atom64_t *atom64 = nullptr;  // (x, y, z, width), n
     float4 *atom32 = nullptr;   // (x, y, z, width), npad (padding: far away, width 1)
+    float4 *atomdf = nullptr;   // 2 per atom: (xh, xl, yh, yl), (zh, zl, width, 0) float pairs
     double *eta = nullptr;      // n
 
     // Kbar CSR (device)

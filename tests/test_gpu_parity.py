@@ -178,6 +178,29 @@ def test_matrix_free_equals_stored_mixed(W, ctx, S):
     assert np.abs(ys - ym).max() <= 1e-4 * np.abs(ys).max()
 
 
+@pytest.mark.parametrize("n,ncplx", [(1000, 2), (1333, 7), (2049, 20), (600, 40)])
+def test_apply_double_float_matrix_free_within_derived_bound(W, ctx, orc, S, n, ncplx):
+    """Matrix-free double-float product: far-pair 1/r from float-pair coordinates with one
+    double-float Newton step on the FP32 rsqrt (entry error ~1e-13 relative), near pairs in
+    FP64.  Per element |dy_i| <= TAU * (sum_p Kbar_ip (s_i + s_j) + |z| |x_i|) with
+    TAU = 1e-12: entry error 1e-13 plus the double-float accumulation of the stored case."""
+    xyz = S.random_cluster(n, seed=n + 9) + 37.0     # away from the origin: tests the coordinate split
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=0)
+    sysm = orc.System(xyz, p)
+    om = S.ev(np.linspace(0.2, 1.9, ncplx))
+    x = S.random_complex((n, ncplx), seed=13)
+    y = np.empty_like(x)
+    g.apply(om, x, y, prec=W.PREC_DF)
+    worst = 0.0
+    for c in range(ncplx):
+        z = sysm.z(om[c])
+        ref = _oracle_apply(orc, sysm, z, x[:, c])
+        worst = max(worst, float(np.max(np.abs(y[:, c] - ref) / _mixed_bound(sysm, z, x[:, c]))))
+    print("matrix-free double-float apply: max |dy| / unit bound =", worst)
+    assert worst <= 1e-12
+
+
 def test_apply_device_pointers_and_stream(W, ctx, orc, S):
     torch = pytest.importorskip("torch")
     n, ncplx = 900, 4
