@@ -49,7 +49,26 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
+    ap.add_argument("--mode", default=None, choices=["solve", "apply"],
+                    help="solve: block solves per second (default); apply: operator applies, "
+                         "pair interactions per second (default for disk1m)")
     return ap.parse_args()
+
+
+# D storage per workload: FP64 + bf16 planes where both fit; bf16 planes only for the 150k
+# sphere (FP64 D would be 180 GB); nothing stored for the 1M-atom disk (matrix-free).
+def store_for(name, wfq):
+    if name == "sphere150k":
+        return wfq.STORE_BF16X2
+    if name in ("disk1m", "disk100k"):
+        return 0
+    return wfq.STORE_FP64 | wfq.STORE_BF16X2
+
+
+# Minimum FP32-pipe instructions to generate one D entry as a bf16 hi/lo pair on the
+# matrix-free path: 3 coordinate differences, 3 for r^2, 1 for sigma^2, 1 far/near test,
+# 1 rsqrt (MUFU), 4 for the split (round, widen, subtract, round).
+MF_OPS_PER_PAIR = 13
 
 
 def load_peaks():
@@ -65,6 +84,10 @@ def workload(name):
     if name == "cnt8k":   # small case for ncu captures: same tube, 205 cells, same block width
         wl = S.workload("cnt20k")
         wl["xyz"] = S.nanotube(10, 10, 205)
+        return wl
+    if name == "disk100k":   # small matrix-free case for ncu captures: same disk family, 18.3 nm
+        wl = S.workload("disk1m")
+        wl["xyz"] = S.graphene_disk(58.0, vacancy_frac=0.01, seed=20210304)
         return wl
     return S.workload(name)
 
@@ -122,6 +145,26 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
+
+# Largest N for which the oracle's CPU baseline stores D (8 N^2 bytes of host memory) and
+# solves sampled columns outright; above it the baseline is the oracle's row-sampled apply
+# throughput, extrapolated to solves/s with the iteration counts of the GPU solve.
+ORACLE_STORED_MAX_N = 25000
+
+
+def oracle_rows_rate(wl, nrows=8):
+    """Pair evaluations per second of the oracle's row-sampled apply (one column)."""
+    from oracle import oracle as orc
+    xyz, p = wl["xyz"], wl["params"]
+    n = len(xyz)
+    rng = np.random.default_rng(11)
+    rows = rng.choice(n, size=nrows, replace=False)
+    x = rng.standard_normal(n) + 0j
+    t0 = time.perf_counter()
+    orc.apply_rows(xyz, p, orc.z_of_omega(wl["omega"][0], p), x, rows)
+    secs = time.perf_counter() - t0
+    return secs, rows
+
 
 def oracle_sample(wl, budget_s, cols):
     """Solve sampled columns with the FP64 oracle (stored D, GMRES(50), rel tol 1e-10).
@@ -190,8 +233,11 @@ def run_ours(args, rank, world, dist):
     n, nf, nd = len(xyz), len(om), len(dirs)
     ncols = nf * nd
     ctx = wfq.Context(local)
-    store = wfq.STORE_FP64 | wfq.STORE_BF16X2
+    store = store_for(args.workload, wfq)
     g = wfq.Geometry(ctx, xyz, p, store=store)
+    mode = args.mode or ("apply" if args.workload in ("disk1m", "disk100k") else "solve")
+    if mode == "apply":
+        return run_apply(args, rank, world, dist, ctx, g, wl, store)
     stream = torch.cuda.current_stream()
     q = torch.empty((n, ncols), dtype=torch.complex128, device="cuda")
 
@@ -309,7 +355,20 @@ def run_ours(args, rank, world, dist):
                       "includes": "geometry build (Kbar CSR, FP64 + bf16 D) from host coordinates, solve, alpha"}
 
     # CPU baseline (oracle, rank 0, N = 1 only) and accuracy audit of sampled columns
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and n > ORACLE_STORED_MAX_N:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        from oracle import build as ob
+        ob.build()
+        secs, rows = oracle_rows_rate(wl)
+        nbr = g.info()["nnz"] / n
+        pairs_per_s = len(rows) * (2.0 + nbr) * n / secs
+        mean_it = float(np.mean(iters))
+        out["cpu_baseline"] = {"value": pairs_per_s / (float(n) * n * mean_it), "unit": "solves/s",
+                               "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"extrapolated: oracle row-sampled apply ({len(rows)} rows, D recomputed "
+                                         f"from Eq. 3) at {pairs_per_s / 1e9:.3f} Gpairs/s, N^2 pairs per apply, "
+                                         f"{mean_it:.1f} applies per solve (mean iterations of this GPU solve)"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and n <= ORACLE_STORED_MAX_N:
         os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
         from oracle import build as ob
         ob.build()
@@ -324,6 +383,113 @@ def run_ours(args, rank, world, dist):
                                          "(D assembly not timed)"}
         out["accuracy"]["alpha_rel_err_vs_oracle_sampled"] = max(errs) if errs else None
         out["accuracy"]["alpha_columns_checked"] = sorted(alphas)
+    g.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_apply(args, rank, world, dist, ctx, g, wl, store):
+    """Operator applies y = (A - z I) x on all columns of the workload at once (mixed
+    precision), timed on device-resident inputs; metric = pair interactions per second
+    (N^2 per apply; one pass over the pairs serves every column)."""
+    import torch
+    from paper_2103_00438_gb300 import wfq
+    xyz, p, om, dirs = wl["xyz"], wl["params"], wl["omega"], wl["dirs"]
+    n = len(xyz)
+    ncplx = len(om) * len(dirs)
+    omc = np.repeat(om, len(dirs))
+    rng = np.random.default_rng(20210303)
+    xh = ((rng.standard_normal((n, ncplx)) + 1j * rng.standard_normal((n, ncplx))) / np.sqrt(2)).astype(np.complex64)
+    x = torch.from_numpy(xh).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.apply(omc, x, y, prec=wfq.PREC_MIXED, stream=stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ctx.profile(True)
+    l0 = wfq.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.apply(omc, x, y, prec=wfq.PREC_MIXED, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = wfq.kernel_launches() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    gemm_n, gemm_ms, gemm_flops = ctx.profile_read(wfq.KT_GEMM_MIXED)
+    ctx.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pairs = float(n) * float(n)
+    value = pairs * args.steps * world / (ms * 1e-3) / 1e9
+    peaks, peak_src = load_peaks()
+    gemm_avg = gemm_ms / max(gemm_n, 1)
+    if store & wfq.STORE_BF16X2:
+        ach = gemm_flops / (gemm_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "gemm_3xbf16 (k_gemm3_tc)", "avg_ms": gemm_avg,
+                "peak_source": peak_src + " bf16_tflops_sustained"}
+    else:
+        props = torch.cuda.get_device_properties(0)
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak_gpairs = props.multi_processor_count * 128 * sm_mhz * 1e6 / MF_OPS_PER_PAIR / 1e9
+        ach = pairs / (gemm_avg * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": peak_gpairs, "unit": "Gpairs/s", "frac": ach / peak_gpairs,
+                "traffic": None, "kernel": "gemm_3xbf16 matrix-free (k_gemm3_mf)", "avg_ms": gemm_avg,
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz / "
+                               f"{MF_OPS_PER_PAIR} instructions per generated D entry",
+                "tensor_tflops": gemm_flops / (gemm_ms * 1e-3) / 1e12}
+    out = {"metric": "T-pair Gint/s", "value": value, "unit": "Gint/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16x3+f32", "data": "synthetic",
+           "config": {"workload": args.workload, "n_atoms": n, "columns": 2 * ncplx,
+                      "path": "stored bf16 D" if store & wfq.STORE_BF16X2 else "matrix-free",
+                      "precision": "mixed: 3xBF16 D products, FP32 accumulation",
+                      "parallelism": f"replicas{world}",
+                      "l2": "inputs larger than L2" if n * n * 4 > 129e6 or n * 64 > 129e6 else "small"},
+           "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
+    # accuracy on sampled rows against the oracle (rows recomputed from Eq. 3 one by one)
+    if rank == 0 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        from oracle import build as ob
+        from oracle import oracle as orc
+        ob.build()
+        if True:
+            yh = y.cpu().numpy()
+            rows = rng.choice(n, size=16, replace=False)
+            t0 = time.perf_counter()
+            yo, bnd = orc.apply_rows(xyz, p, orc.z_of_omega(omc[0], p), xh[:, 0].astype(complex), rows)
+            secs = time.perf_counter() - t0
+            ratio = float(np.max(np.abs(yh[rows, 0] - yo) / bnd))
+            # pair evaluations the oracle made: a neighbour scan per row plus one N-term row
+            # of D for the row and for each neighbour (~49 neighbours in graphene)
+            g_info = g.info()
+            nbr = g_info["nnz"] / n
+            row_pairs = float(len(rows)) * (2.0 + nbr) * n
+            out["accuracy"] = {"sampled_rows": len(rows), "max_err_over_bound": ratio, "bound_tolerance": 4e-5}
+            out["cpu_baseline"] = {"value": row_pairs / secs / 1e9, "unit": "Gint/s", "cores": os.cpu_count(),
+                                   "kind": "oracle",
+                                   "sample": f"{len(rows)} rows of (A - zI)x with D recomputed from Eq. 3 for each "
+                                             "row and its neighbours (one column)"}
+    if not args.no_e2e:
+        yh2 = np.empty_like(xh)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.apply(omc, xh, yh2, prec=wfq.PREC_MIXED)
+        te = time.perf_counter() - t0
+        out["e2e"] = {"value": pairs * args.steps * world / te / 1e9, "unit": "Gint/s",
+                      "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
     g.close()
     ctx.close()
     if rank == 0:

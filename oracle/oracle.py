@@ -57,6 +57,7 @@ def lib():
         L.orc_residual_norm.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _P]
         L.orc_residual_norm.restype = _D
         L.orc_vdot.argtypes = [_I64, _P, _P, _P]
+        L.orc_apply_rows.argtypes = [_I64, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _I64, _P, _P, _P]
         _lib = L
     return _lib
 
@@ -273,6 +274,22 @@ def alpha(xyz, q, E0=1.0):
     out = np.empty(6)
     lib().orc_alpha(len(xyz), _ptr(xyz), _ptr(q), float(E0), _ptr(out))
     return out[0::2] + 1j * out[1::2]
+
+
+def apply_rows(xyz, p, z, x, rows, eta=None):
+    """Selected rows of (A - zI) x with D recomputed from Eq. 3 and each row's neighbours
+    found by a brute-force scan (no N x N storage, no CSR), plus the per-row rounding
+    scale sum_p Kbar_ip (s_i + s_j) + |z||x_i|, s = |D||x|."""
+    xyz = _f64(xyz)
+    n = len(xyz)
+    eta = _eta_vec(n, p["eta"] if eta is None else eta)
+    x = _c128(x)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    y = np.empty(len(rows), dtype=np.complex128)
+    bound = np.empty(len(rows))
+    lib().orc_apply_rows(n, _ptr(xyz), _ptr(eta), p["r0"], p["d_fermi"], p["s_fermi"], p["area"],
+                         p["cutoff_eps"], z.real, z.imag, _ptr(x), len(rows), _ptr(rows), _ptr(y), _ptr(bound))
+    return y, bound
 
 
 def vdot(u, v):

@@ -602,8 +602,9 @@ __global__ void __launch_bounds__(256) k_split_bf16(int64_t n, int64_t npad, int
     }
 }
 
-// Rows of the bf16 X planes: the real columns rounded up to whole 64-column GEMM tiles.
-static int64_t mixed_cpad(int64_t cc) { return round_up(2 * cc, 64); }
+// Rows of the bf16 X planes: the real columns rounded up to 32 (the accumulator is read
+// back from tensor memory in 32-column chunks; MMA N is a multiple of 16).
+static int64_t mixed_cpad(int64_t cc) { return round_up(2 * cc, 32); }
 
 size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc) {
     int64_t cpad = mixed_cpad(cc);

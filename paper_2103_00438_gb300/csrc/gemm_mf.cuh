@@ -3,14 +3,16 @@
 // instead of being read from a stored matrix, then contracted with the three bf16
 // products of gemm_tc.cuh.
 //
-// Roles (10 warps):
-//   warp 0    : TMEM allocation; one lane loads the Xhi / Xlo stage tiles by TMA.
-//   warp 1    : one lane issues tcgen05.mma (three products per 16-atom K step).
-//   warps 2-9 : generate the 128 x 32 D tile of every stage -- one row per thread and half
-//               a row (16 atoms) per warp-pair half -- as bf16 hi and lo, written straight
-//               into the 64-byte-swizzled K-major layout the MMA descriptors expect; then
-//               a proxy fence and one arrival per warp on the stage's full-barrier.
-//   warps 2-5 : also the epilogue (TMEM -> registers -> U), as in gemm_tc.cuh.
+// Roles (18 warps):
+//   warp 0     : TMEM allocation; one lane loads, per stage, the Xhi / Xlo tiles (TMA) and
+//                the 32 atom records of the stage's K block (bulk copy, own barrier).
+//   warp 1     : one lane issues tcgen05.mma (three products per 16-atom K step).
+//   warps 2-17 : generate the 128 x 32 D tile of every stage -- one row per thread, one
+//                16-byte chunk (8 atoms) per group of four warps -- as bf16 hi and lo,
+//                written straight into the 64-byte-swizzled K-major layout the MMA
+//                descriptors expect; then a proxy fence and one arrival per warp on the
+//                stage's full-barrier.
+//   warps 2-5  : also the epilogue (TMEM -> registers -> U), as in gemm_tc.cuh.
 // Work split and waits are those of gemm_tc.cuh (stream-K over (row tile, k block) units,
 // at most two CTAs per tile, bounded barrier waits).
 #pragma once
@@ -20,7 +22,8 @@
 namespace wfq {
 namespace tc {
 
-constexpr int MF_GEN_WARPS = 8;
+constexpr int MF_GEN_WARPS = 16;
+constexpr uint32_t MF_ATOM_BYTES = BK * 16;   // 32 float4 atom records per stage
 constexpr int MF_THREADS = 64 + 32 * MF_GEN_WARPS;
 
 struct MfParams {
@@ -43,6 +46,12 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) 
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(MF_THREADS, 1)
     k_gemm3_mf(const __grid_constant__ CUtensorMap tm_xhi, const __grid_constant__ CUtensorMap tm_xlo,
                const MfParams mp) {
@@ -55,8 +64,10 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
     uint64_t *acc_full = empty + MAX_STAGES;
     uint64_t *acc_empty = acc_full + 1;
     uint64_t *drain = acc_empty + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *atoms_full = drain + 1;   // MAX_STAGES barriers: k-atom records landed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(atoms_full + MAX_STAGES);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const uint32_t atoms_off = 2 * A_BYTES + 2 * p.b_bytes;   // k-atom records inside a stage
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t G = gridDim.x;
@@ -67,6 +78,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
         for (int s = 0; s < p.stages; ++s) {
             mbar_init(smem_u32(full + s), 1 + MF_GEN_WARPS);
             mbar_init(smem_u32(empty + s), 1);
+            mbar_init(smem_u32(atoms_full + s), 1);
         }
         mbar_init(smem_u32(acc_full), 1);
         mbar_init(smem_u32(acc_empty), 4);
@@ -104,6 +116,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
                 const int kb = (int)(u % p.kblocks);
                 const uint32_t base = smem_base + (uint32_t)s * p.stage_bytes;
                 const uint32_t fb = smem_u32(full + s);
+                const uint32_t ab = smem_u32(atoms_full + s);
+                mbar_expect_tx(ab, MF_ATOM_BYTES);
+                bulk_load(base + atoms_off, mp.atoms + (int64_t)kb * BK, MF_ATOM_BYTES, ab);
                 mbar_expect_tx(fb, b_tx);
                 for (int j = 0; j < p.nsplit; ++j) {
                     tma_load_2d(base + 2 * A_BYTES + (uint32_t)(j * p.nchunk * ROWB), &tm_xhi, fb, kb * BK,
@@ -117,7 +132,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
                 for (int s = 0; s < p.stages; ++s)
                     if (last_it[s] >= 0) {
                         volatile int no_abort = 0;
-                        mbar_wait(smem_u32(full + s), (uint32_t)((last_it[s] / p.stages) & 1), p, 1, &no_abort);
+                        const uint32_t par = (uint32_t)((last_it[s] / p.stages) & 1);
+                        mbar_wait(smem_u32(atoms_full + s), par, p, 1, &no_abort);
+                        mbar_wait(smem_u32(full + s), par, p, 1, &no_abort);
                     }
         }
     } else if (warp == 1) {
@@ -170,9 +187,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
         }
     } else {
         // ---------------------------------------------------------- D-tile generators
-        const int gt = threadIdx.x - 64;           // 0..255
+        const int gt = threadIdx.x - 64;           // 0..511
         const int row = gt & (BM - 1);             // tile row of this thread
-        const int half = gt >> 7;                  // which 16 atoms of the 32-atom stage
+        const int kc = gt >> 7;                    // 16-byte chunk (8 atoms) of the 64-byte row
         const bool epi = warp < 6;                 // warps 2-5 also run the epilogue
         const int quad = warp & 3;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
@@ -186,37 +203,64 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
             const int64_t tile = u / p.kblocks;
             const int64_t seg_end = u_end < (tile + 1) * p.kblocks ? u_end : (tile + 1) * p.kblocks;
             const int64_t seg_begin = u;
-            const int64_t gi = tile * BM + row;
+            const int gi = (int)(tile * BM + row);
             const float4 ai = mp.atoms[gi];
             const bool row_ok = gi < p.n;
             const float wa2 = ai.w * ai.w;
+            const float eta_i = eta_from_w / ai.w;
             for (; u < seg_end; ++u, ++it) {
                 const int s = (int)(it % p.stages);
                 const uint32_t ph = (uint32_t)((it / p.stages) & 1);
-                if (!mbar_wait(smem_u32(empty + s), ph ^ 1u, p, 6, abort_flag)) {
+                // the k-atom records land only after the stage was released by the MMAs,
+                // so this one wait covers both
+                if (!mbar_wait(smem_u32(atoms_full + s), ph, p, 6, abort_flag)) {
                     aborted = true;
                     break;
                 }
-                const int64_t k0 = (u % p.kblocks) * BK;
+                const int k0 = (int)(u % p.kblocks) * BK;
                 const uint32_t base = smem_base + (uint32_t)s * p.stage_bytes;
+                const float4 *atoms_s = reinterpret_cast<const float4 *>(smem + (size_t)s * p.stage_bytes + atoms_off);
+                {
+                    const int kb0 = k0 + kc * 8;
+                    float dv[8], r2v[8], s2v[8], rinv[8];
+                    uint32_t near = 0;
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int kc = half * 2 + q;   // 16-byte chunk (8 atoms) of the 64-byte row
+                    for (int e = 0; e < 8; ++e) {
+                        // far pairs: 1/r from one rsqrt (erf(r/sigma) rounds to 1 in FP32)
+                        const float4 b = atoms_s[kc * 8 + e];
+                        const float dx = ai.x - b.x, dy = ai.y - b.y, dz = ai.z - b.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float s2 = wa2 + b.w * b.w;
+                        const float ri = rsqrtf(r2);
+                        r2v[e] = r2;
+                        s2v[e] = s2;
+                        rinv[e] = ri;
+                        dv[e] = ri;
+                        near |= (r2 < 16.0f * s2 ? 1u : 0u) << e;
+                    }
+                    // near pairs (rare: only tiles close to the diagonal) take the erf branch,
+                    // entered by a warp only when one of its lanes needs it
+                    if (__any_sync(0xffffffffu, near != 0u)) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (near & (1u << e)) dv[e] = erff(r2v[e] * rinv[e] * rsqrtf(s2v[e])) * rinv[e];
+                    }
+                    if (gi >= kb0 && gi < kb0 + 8) {                      // D_ii = eta_i
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (gi == kb0 + e) dv[e] = eta_i;
+                    }
+                    if (!row_ok || kb0 + 8 > p.n) {                       // padding rows / columns
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (!row_ok || kb0 + e >= p.n) dv[e] = 0.f;
+                    }
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
-                        float dv[2];
-#pragma unroll
-                        for (int t = 0; t < 2; ++t) {
-                            const int64_t gk = k0 + kc * 8 + e + t;
-                            float d = 0.f;
-                            if (row_ok && gk < p.n)
-                                d = (gk == gi) ? eta_from_w / ai.w : d_pair_f32(ai, mp.atoms[gk], wa2);
-                            dv[t] = d;
-                        }
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(dv[0]), h1 = __float2bfloat16_rn(dv[1]);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(dv[0] - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(dv[1] - __bfloat162float(h1));
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(dv[e]), h1 = __float2bfloat16_rn(dv[e + 1]);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(dv[e] - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(dv[e + 1] - __bfloat162float(h1));
                         hw[e >> 1] = pack_bf16(h0, h1);
                         lw[e >> 1] = pack_bf16(l0, l1);
                     }
@@ -298,7 +342,7 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
     p.nsplit = (cpad + 255) / 256;
     p.nchunk = cpad / p.nsplit;
     p.b_bytes = (uint32_t)cpad * ROWB;
-    p.stage_bytes = 2 * A_BYTES + 2 * p.b_bytes;
+    p.stage_bytes = (2 * A_BYTES + 2 * p.b_bytes + MF_ATOM_BYTES + 1023) / 1024 * 1024;
     p.stages = (int)((kMaxDynSmem - 2048) / p.stage_bytes);
     if (p.stages > MAX_STAGES) p.stages = MAX_STAGES;
     int tcols = 32;
@@ -316,7 +360,7 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
     if (!make_map(&m_xhi, Xhi, npad, cpad, npad, p.nchunk, msg) || !make_map(&m_xlo, Xlo, npad, cpad, npad, p.nchunk, msg))
         return cudaErrorInvalidValue;
     const int64_t grid = grid_size(mtiles, num_sms);
-    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 256;
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 512;
     cudaError_t e = cudaFuncSetAttribute(k_gemm3_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_gemm3_mf<<<(unsigned)grid, MF_THREADS, smem, s>>>(m_xhi, m_xlo, mp);
@@ -326,7 +370,7 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
 inline cudaError_t gemm3_mf(const float4 *atoms, int64_t n, int64_t npad, const __nv_bfloat16 *Xhi,
                             const __nv_bfloat16 *Xlo, int64_t cpad, float *U, int64_t ldu, int num_sms, int *err,
                             cudaStream_t s, int *launches, std::string *msg) {
-    if (npad % BM != 0 || cpad % 64 != 0 || cpad < ldu || ldu < 1) {
+    if (npad % BM != 0 || cpad % 32 != 0 || cpad < ldu || ldu < 1) {
         if (msg) *msg = "gemm_mf: bad shape";
         return cudaErrorInvalidValue;
     }

@@ -47,7 +47,7 @@ struct Params {
     int64_t ncols;     // valid columns of U in this launch
     int64_t units;     // mtiles * kblocks
     int kblocks;       // npad / BK
-    int cpad;          // accumulator columns (multiple of 64, <= 512)
+    int cpad;          // accumulator columns (multiple of 32, <= 512)
     int nsplit;        // MMA instructions across N
     int nchunk;        // columns per MMA instruction (multiple of 16, <= 256)
     int stages;
@@ -457,7 +457,7 @@ inline cudaError_t launch_group(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *D
 inline cudaError_t gemm3_tc(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *Dlo, int64_t n, int64_t npad,
                             const __nv_bfloat16 *Xhi, const __nv_bfloat16 *Xlo, int64_t cpad, float *U, int64_t ldu,
                             int num_sms, int *err, cudaStream_t s, int *launches, std::string *msg) {
-    if (npad % BM != 0 || cpad % 64 != 0 || cpad < ldu || ldu < 1) {
+    if (npad % BM != 0 || cpad % 32 != 0 || cpad < ldu || ldu < 1) {
         if (msg) *msg = "gemm_tc: bad shape";
         return cudaErrorInvalidValue;
     }

@@ -138,6 +138,19 @@ def test_operator_kinds_agree(orc, S):
     assert np.abs(y_otf - y_dense).max() <= 1e-13 * scale
 
 
+def test_apply_rows_equals_full_apply(orc, S):
+    xyz = S.random_cluster(150, seed=8)
+    p = _params(S, r0=2.7)
+    sysm = orc.System(xyz, p)
+    z = sysm.z(S.ev(0.9))
+    x = S.random_complex(150, seed=2)
+    full = orc.Operator.dense(sysm.A).apply(z, x)
+    rows = np.array([0, 7, 77, 149])
+    y, bound = orc.apply_rows(xyz, dict(p, cutoff_eps=0.0), z, x, rows)
+    assert np.abs(y - full[rows]).max() <= 1e-13 * np.abs(full).max()
+    assert np.all(bound >= np.abs(full[rows]))
+
+
 # --------------------------------------------------------------------- closed forms
 
 def test_dimer_closed_form(orc, S):
