@@ -92,6 +92,20 @@ def workload(name):
     return S.workload(name)
 
 
+# ------------------------------------------------------------------ replicas
+
+def max_over_ranks(value, dist):
+    """Max of a per-rank float over all ranks (the whole-job time of weak-scaled replicas);
+    identity without a process group.  Uses a CUDA tensor under NCCL, a CPU one otherwise."""
+    if dist is None:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -281,10 +295,7 @@ def run_ours(args, rank, world, dist):
     or_n, or_ms, _ = ctx.profile_read(wfq.KT_ORTHO)
     rs_n, rs_ms, _ = ctx.profile_read(wfq.KT_RESIDUAL)
     ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
 
     st_last, status_last = stats_all[-1]
     max_res = max(s["rel_residual"] for st, _ in stats_all for s in st)
@@ -345,10 +356,7 @@ def run_ours(args, rank, world, dist):
             ge.close()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(te, dist)
         out["e2e"] = {"value": good_cols * args.steps * world / te, "unit": "solves/s",
                       "h2d_bytes_per_step": int(xyz.nbytes + om.nbytes + dirs.nbytes),
                       "d2h_bytes_per_step": int(n * ncols * 16 + ncols * 3 * 16),
@@ -426,10 +434,7 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
     ms = ev0.elapsed_time(ev1)
     gemm_n, gemm_ms, gemm_flops = ctx.profile_read(wfq.KT_GEMM_MIXED)
     ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     pairs = float(n) * float(n)
     value = pairs * args.steps * world / (ms * 1e-3) / 1e9
     peaks, peak_src = load_peaks()

@@ -242,6 +242,42 @@ int wfq_solve_qmr(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
 int wfq_polarizability(wfq_geom *g, int64_t ncols, const double *q, double E0,
                        double *alpha, void *stream);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A request server on one context: `nworkers` threads, each with its own CUDA stream,
+ * take solve requests from a FIFO queue.  Structures stay resident (requests reference
+ * geometries built with wfq_build_geometry; a geometry must outlive its requests).
+ * A worker that becomes free takes the oldest request whose batch fits the memory budget
+ * and merges into the same block solve every queued request on the same geometry with
+ * the same settings (continuous batching), up to max_columns complex columns; batches on
+ * different workers run concurrently.  Solves are mixed-precision GMRES(m) with FP64
+ * refinement (as wfq_solve_gmres with WFQ_PREC_MIXED).
+ *   budget_bytes: device memory the batches in flight may use together (Krylov bases,
+ *   blocks, scratch; the geometries themselves are not counted).  A batch that alone
+ *   exceeds it still runs when nothing else is in flight. */
+typedef struct wfq_server wfq_server;
+int wfq_server_create(wfq_ctx *ctx, int nworkers, int64_t budget_bytes, int max_columns,
+                      wfq_server **out);
+
+/* Queues one request: nfreq frequencies x ndir directions (columns c = f * ndir + d, as in
+ * wfq_solve_gmres).  q_host (N x ncols complex128) and stats (ncols, or NULL) are host
+ * buffers the caller keeps valid until the request is complete; the server writes them.
+ * Returns at once with *request_id.  WFQ_ENOMEM if the request alone cannot fit the budget,
+ * WFQ_ESINGULAR for omega = 0. */
+int wfq_server_submit(wfq_server *s, wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
+                      const double *dirs, double E0, int m, double rel_tol, int max_iter,
+                      double *q_host, wfq_stats *stats, int64_t *request_id);
+
+/* State of a request; wait != 0 blocks until it is complete.  When complete: status
+ * (WFQ_OK, WFQ_ENOCONV or an error), latency_s (submit -> completion), queue_s (submit ->
+ * start of its batch), batch_columns (columns of the block solve it ran in), and the
+ * request is released (its id becomes unknown).  Any out-pointer may be NULL. */
+int wfq_server_poll(wfq_server *s, int64_t request_id, int wait, int *done, int *status,
+                    double *latency_s, double *queue_s, int *batch_columns);
+
+/* Finishes every queued request, then stops the workers and frees the server. */
+int wfq_server_destroy(wfq_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -212,6 +212,12 @@ struct SolveArgs {
     const double *omega = nullptr;  // host
     int ndir = 0;
     const double *dirs = nullptr;   // host, ndir x 3
+    // Optional explicit column list (used by the server when it merges requests): column
+    // c solves at frequency col_omega[c] with field direction dirs[col_dir[c]]; ncols columns.
+    // When null, the columns are the product nfreq x ndir (c = f * ndir + d).
+    const double *col_omega = nullptr;
+    const int *col_dir = nullptr;
+    int64_t ncols = 0;
     double E0 = 1.0;
     int m = 0;
     double rel_tol = 1e-8;
@@ -224,6 +230,9 @@ struct SolveArgs {
 
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
 int solve_qmr(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
+
+// Device bytes a block solve of `cc` columns allocates (Krylov basis, FP64 blocks, scratch).
+size_t solve_footprint(const wfq_geom *g, int64_t cc, int m, int prec);
 
 // z(omega) of Eq. 12 for the geometry's parameters.
 inline double2 z_of_omega(const wfq_params &p, double omega) {

@@ -415,13 +415,13 @@ __global__ void k_residual(uint32_t total, const double2 *__restrict__ B, const 
     if (e < total) r[e] = csub(B[e], Y[e]);
 }
 
-// B[i][f*ndir + d] = R[i][d]
-__global__ void k_make_b(uint32_t total, uint32_t cc, int ndir, const double *__restrict__ R,
-                         double2 *__restrict__ B) {
+// B[i][c] = R[i][col_dir[c]]
+__global__ void k_make_b(uint32_t total, uint32_t cc, int ndir, const int *__restrict__ col_dir,
+                         const double *__restrict__ R, double2 *__restrict__ B) {
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= total) return;
     const uint32_t i = e / cc, c = e % cc;
-    B[e] = make_double2(R[(int64_t)i * ndir + (int)(c % (uint32_t)ndir)], 0.0);
+    B[e] = make_double2(R[(int64_t)i * ndir + col_dir[c]], 0.0);
 }
 
 // v0 = r / ||r|| (zero for columns marked done)
@@ -476,11 +476,11 @@ __global__ void k_backsolve(int64_t na, int jlast, GmresDev st, double2 *__restr
     }
 }
 
-__global__ void k_set_z(int64_t cc, int ndir, const double *__restrict__ omega, double n0, double tau,
+__global__ void k_set_z(int64_t cc, const double *__restrict__ col_omega, double n0, double tau,
                         double2 *__restrict__ z) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cc) return;
-    const double w = omega[c / ndir];
+    const double w = col_omega[c];
     const double f = -w / (2.0 * n0 * tau);
     z[c] = make_double2(f * w * tau, f);
 }
@@ -494,7 +494,7 @@ struct Common {
     int num_sms = 1;
     DevBuf<double2> B, z, partial, bnorm, rnorm, tmp;
     DevBuf<double> R, dirs, omega;
-    DevBuf<int> idx;
+    DevBuf<int> idx, coldir;
     // per-cycle compacted FP64 buffers (sized for all columns)
     DevBuf<double2> Ba, xa, ra, Ya, Ua, za;
     DevBuf<double> bnorm_a;
@@ -505,7 +505,13 @@ struct Common {
         g = geom;
         s = stream;
         n = g->n;
-        cc = a.nfreq * a.ndir;
+        cc = a.col_omega ? a.ncols : a.nfreq * a.ndir;
+        std::vector<double> om_c(cc);
+        std::vector<int> dir_c(cc);
+        for (int64_t c = 0; c < cc; ++c) {
+            om_c[c] = a.col_omega ? a.col_omega[c] : a.omega[c / a.ndir];
+            dir_c[c] = a.col_dir ? a.col_dir[c] : (int)(c % a.ndir);
+        }
         num_sms = g->ctx->num_sms;
         if ((double)n * (double)cc * 2.0 >= 2147483647.0)
             return fail(WFQ_EUNSUPPORTED, "n * columns too large for one block (>= 2^30)");
@@ -520,8 +526,9 @@ struct Common {
         WFQ_TRY(tmp.alloc(ctx, (size_t)cc * MAX_GROUP, s));
         WFQ_TRY(R.alloc(ctx, n * a.ndir, s));
         WFQ_TRY(dirs.alloc(ctx, 3 * a.ndir, s));
-        WFQ_TRY(omega.alloc(ctx, a.nfreq, s));
+        WFQ_TRY(omega.alloc(ctx, cc, s));
         WFQ_TRY(idx.alloc(ctx, cc, s));
+        WFQ_TRY(coldir.alloc(ctx, cc, s));
         WFQ_TRY(Ba.alloc(ctx, n * cc, s));
         WFQ_TRY(xa.alloc(ctx, n * cc, s));
         WFQ_TRY(ra.alloc(ctx, n * cc, s));
@@ -530,11 +537,12 @@ struct Common {
         WFQ_TRY(za.alloc(ctx, cc, s));
         WFQ_TRY(bnorm_a.alloc(ctx, cc, s));
         WFQ_CUDA(cudaMemcpyAsync(dirs.ptr, a.dirs, sizeof(double) * 3 * a.ndir, cudaMemcpyHostToDevice, s));
-        WFQ_CUDA(cudaMemcpyAsync(omega.ptr, a.omega, sizeof(double) * a.nfreq, cudaMemcpyHostToDevice, s));
-        k_set_z<<<nblocks(cc), 256, 0, s>>>(cc, a.ndir, omega.ptr, g->p.n0, g->p.tau, z.ptr); note_launch();
+        WFQ_CUDA(cudaMemcpyAsync(omega.ptr, om_c.data(), sizeof(double) * cc, cudaMemcpyHostToDevice, s));
+        WFQ_CUDA(cudaMemcpyAsync(coldir.ptr, dir_c.data(), sizeof(int) * cc, cudaMemcpyHostToDevice, s));
+        k_set_z<<<nblocks(cc), 256, 0, s>>>(cc, omega.ptr, g->p.n0, g->p.tau, z.ptr); note_launch();
         WFQ_CUDA(cudaGetLastError());
         WFQ_TRY(launch_rhs(g, a.ndir, dirs.ptr, a.E0, R.ptr, s));
-        k_make_b<<<nblocks(n * cc), 256, 0, s>>>((uint32_t)(n * cc), (uint32_t)cc, a.ndir, R.ptr, B.ptr); note_launch();
+        k_make_b<<<nblocks(n * cc), 256, 0, s>>>((uint32_t)(n * cc), (uint32_t)cc, a.ndir, coldir.ptr, R.ptr, B.ptr); note_launch();
         WFQ_CUDA(cudaGetLastError());
         WFQ_TRY(colnorm(B.ptr, cc, bnorm.ptr));
         bn_h.assign(cc, 0.0);
@@ -609,6 +617,36 @@ struct Common {
         WFQ_CUDA(cudaStreamSynchronize(s));   // sub lives on this stack frame
         act = keep;
         return select(act);
+    }
+
+    // ra = Ba - (A - z I) xa with the mixed operator (xa rounded to complex64): the restart
+    // residual of a cycle whose columns are all still far from the tolerance, where its
+    // ~1e-6 relative error is irrelevant.  Never used to declare convergence.
+    int mixed_residual(const double2 *x, int64_t na, float2 *xs, float2 *u32, float2 *y32, void *scratch) {
+        KScope ks(g->ctx, WFQ_KT_RESIDUAL, s);
+        const uint32_t tot = (uint32_t)(n * na);
+        k_gather<float2, double2><<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)na, cc, idx.ptr, x, xs); note_launch();
+        WFQ_TRY(d_apply_mixed(g, na, xs, u32, scratch, s));
+        WFQ_TRY(sparse_shift_fp32(g, na, u32, xs, za.ptr, y32, s));
+        k_gather<double2, float2><<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)na, na, idx_identity(na), y32, Ya.ptr); note_launch();
+        k_residual<<<nblocks(tot), 256, 0, s>>>(tot, Ba.ptr, Ya.ptr, ra.ptr); note_launch();
+        WFQ_CUDA(cudaGetLastError());
+        return colnorm(ra.ptr, na, rnorm.ptr);
+    }
+
+    // identity column map 0..na-1 (for widening a complex64 block to FP64)
+    DevBuf<int> ident;
+    int64_t ident_n = 0;
+    const int *idx_identity(int64_t na) {
+        if (ident_n < na) {
+            std::vector<int> h(cc);
+            for (int64_t k = 0; k < cc; ++k) h[k] = (int)k;
+            if (!ident.ptr) ident.alloc(g->ctx, cc, s);
+            cudaMemcpyAsync(ident.ptr, h.data(), sizeof(int) * cc, cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);
+            ident_n = cc;
+        }
+        return ident.ptr;
     }
 
     // Host copy of rnorm for the na active columns; records each column's relative
@@ -691,16 +729,30 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     std::vector<int> act(cc), still;
     for (int64_t c = 0; c < cc; ++c) act[c] = (int)c;
     std::vector<int> iters_h(cc, 0), it_a, done_h;
+    DevBuf<float2> xs32, y32;
+    if (mixed) {
+        WFQ_TRY(xs32.alloc(ctx, n * cc, s));
+        WFQ_TRY(y32.alloc(ctx, n * cc, s));
+    }
     int total = 0, cycles = 0;
     // x0 = 0: the first residual is R itself
     WFQ_TRY(cm.select(act));
     WFQ_CUDA(cudaMemcpyAsync(cm.ra.ptr, cm.Ba.ptr, sizeof(double2) * n * cc, cudaMemcpyDeviceToDevice, s));
     WFQ_TRY(cm.colnorm(cm.ra.ptr, cc, cm.rnorm.ptr));
+    bool exact = true;   // the current residual block was computed to FP64 accuracy
+    std::vector<double2> g_h;
+    std::vector<int> jd_h;
 
     for (;;) {
-        WFQ_TRY(cm.classify(act, a.rel_tol, still));
-        if (still.empty() || total >= a.max_iter) break;
-        if (still.size() != act.size()) WFQ_TRY(cm.narrow(act, still));
+        if (exact) {
+            WFQ_TRY(cm.classify(act, a.rel_tol, still));
+            if (still.empty() || total >= a.max_iter) break;
+            if (still.size() != act.size()) WFQ_TRY(cm.narrow(act, still));
+        } else if (total >= a.max_iter) {
+            WFQ_TRY(cm.true_residual(a.q, (int64_t)act.size()));   // final statistics are exact
+            WFQ_TRY(cm.classify(act, a.rel_tol, still));
+            break;
+        }
         const int64_t na = (int64_t)act.size();
         // ---- one restart cycle on the na active columns
         const uint32_t tot = (uint32_t)(n * na);
@@ -767,10 +819,45 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         WFQ_CUDA(cudaStreamSynchronize(s));
         for (int64_t k = 0; k < na; ++k) iters_h[act[k]] += it_a[k];
         ++cycles;
-        // the next cycle (and the convergence test) starts from the FP64 true residual
-        WFQ_TRY(cm.true_residual(a.q, na));
+        // Next residual.  Mixed solves whose columns all ended this cycle with a residual
+        // estimate above 1e-3 ||R|| restart from the mixed-operator residual; otherwise (and
+        // always for FP64 solves) from the FP64-accurate true residual, which alone decides
+        // convergence.
+        bool far = false;
+        if (mixed && jlast >= 0) {
+            g_h.resize((size_t)(m + 1) * na);
+            jd_h.resize(na);
+            WFQ_CUDA(cudaMemcpyAsync(g_h.data(), gv.ptr, sizeof(double2) * (m + 1) * na, cudaMemcpyDeviceToHost, s));
+            WFQ_CUDA(cudaMemcpyAsync(jd_h.data(), jdone.ptr, sizeof(int) * na, cudaMemcpyDeviceToHost, s));
+            WFQ_CUDA(cudaStreamSynchronize(s));
+            far = true;
+            for (int64_t k = 0; k < na && far; ++k) {
+                const double2 gk = g_h[(size_t)jd_h[k] * na + k];
+                const double est = std::sqrt(gk.x * gk.x + gk.y * gk.y);
+                if (!(est > 1e-3 * cm.bn_h[act[k]])) far = false;
+            }
+        }
+        if (far) {
+            WFQ_TRY(cm.mixed_residual(a.q, na, xs32.ptr, U32.ptr, y32.ptr, scratch.ptr));
+            exact = false;
+        } else {
+            WFQ_TRY(cm.true_residual(a.q, na));
+            exact = true;
+        }
     }
     return finish_stats(a, cm, iters_h, cycles, {});
+}
+
+size_t solve_footprint(const wfq_geom *g, int64_t cc, int m, int prec) {
+    const size_t n = (size_t)g->n, nc = n * (size_t)cc;
+    const bool mixed = (prec == WFQ_PREC_MIXED);
+    const size_t vt = mixed ? sizeof(float2) : sizeof(double2);
+    size_t b = (size_t)(m + 1) * nc * vt;                       // Krylov basis
+    b += 8 * nc * sizeof(double2);                              // B, FP64 active blocks, output
+    b += (size_t)(m + 2) * (size_t)(m + 1) * cc * 48;           // Hessenberg, rotations
+    b += (size_t)std::min<int64_t>((int64_t)(n + 127) / 128, 304) * cc * 64 * sizeof(double2);  // partials
+    if (mixed) b += 3 * nc * sizeof(float2) + (size_t)round_up(2 * cc, 32) * (size_t)g->npad * 4;
+    return b;
 }
 
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {

@@ -22,7 +22,8 @@ PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2
 # every symbol include/wfq.h declares
 EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry", "wfq_free_geometry",
            "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_qmr",
-           "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc"]
+           "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc",
+           "wfq_server_create", "wfq_server_submit", "wfq_server_poll", "wfq_server_destroy"]
 KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE, KT_ORTHO, KT_RESIDUAL = 0, 1, 2, 3, 4
 
 
@@ -72,6 +73,11 @@ def load(path: str | None = None):
     L.wfq_solve_qmr.argtypes = [_P, I64, _P, INT, _P, D, D, INT, INT, INT, _P, _P, _P]
     L.wfq_polarizability.argtypes = [_P, I64, _P, D, _P, _P]
     L.wfq_apply_mixed_noalloc.argtypes = [_P, I64, _P, _P, _P, _P]
+    L.wfq_server_create.argtypes = [_P, INT, I64, INT, ctypes.POINTER(_P)]
+    L.wfq_server_submit.argtypes = [_P, _P, I64, _P, INT, _P, D, INT, D, INT, _P, _P, ctypes.POINTER(I64)]
+    L.wfq_server_poll.argtypes = [_P, I64, INT, ctypes.POINTER(INT), ctypes.POINTER(INT), ctypes.POINTER(D),
+                                  ctypes.POINTER(D), ctypes.POINTER(INT)]
+    L.wfq_server_destroy.argtypes = [_P]
     L.wfq_profile.argtypes = [_P, INT]
     L.wfq_profile_read.argtypes = [_P, INT, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
     for name in EXPORTS:
@@ -236,3 +242,51 @@ class Geometry:
         out = np.empty((ncols, 3), dtype=np.complex128)
         _check(_lib.wfq_polarizability(self.h, ncols, _ptr(q), float(E0), _ptr(out), _stream_handle(stream)))
         return out
+
+
+class Server:
+    """wfq_server_*: continuous-batching request server over resident geometries."""
+
+    def __init__(self, ctx: Context, nworkers: int = 3, budget_bytes: int = 64 << 30, max_columns: int = 384):
+        h = _P()
+        _check(_lib.wfq_server_create(ctx.h, int(nworkers), int(budget_bytes), int(max_columns), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, geom: Geometry, omega, dirs, E0=1.0, m=50, rel_tol=1e-8, max_iter=4000):
+        """Queue a request; returns its id.  The result arrays live until poll() returns them."""
+        om = _host_f64(np.atleast_1d(omega))
+        d = _host_f64(np.atleast_2d(dirs))
+        ncols = len(om) * len(d)
+        q = np.empty((geom.n, ncols), dtype=np.complex128)
+        stats = (Stats * ncols)()
+        rid = ctypes.c_int64()
+        _check(_lib.wfq_server_submit(self.h, geom.h, len(om), _ptr(om), len(d), _ptr(d), float(E0), int(m),
+                                      float(rel_tol), int(max_iter), _ptr(q), ctypes.cast(stats, _P),
+                                      ctypes.byref(rid)))
+        self._keep[rid.value] = (q, stats, om, d)
+        return rid.value
+
+    def poll(self, rid: int, wait: bool = True):
+        """None while running; else dict(status, latency_s, queue_s, batch_columns, q, stats)."""
+        done, st, lat, qs, bc = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        _check(_lib.wfq_server_poll(self.h, int(rid), 1 if wait else 0, ctypes.byref(done), ctypes.byref(st),
+                                    ctypes.byref(lat), ctypes.byref(qs), ctypes.byref(bc)))
+        if not done.value:
+            return None
+        q, stats, _, _ = self._keep.pop(rid)
+        return {"status": STATUS.get(st.value, st.value), "latency_s": lat.value, "queue_s": qs.value,
+                "batch_columns": bc.value, "q": q,
+                "stats": [{"iters": s.iters, "rel_residual": s.rel_residual,
+                           "status": STATUS.get(s.status, s.status)} for s in stats]}
+
+    def close(self):
+        if self.h:
+            _check(_lib.wfq_server_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

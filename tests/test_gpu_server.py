@@ -1,0 +1,63 @@
+"""Serving: requests submitted at once over several resident structures are merged into
+block solves (continuous batching) and run on concurrent streams; every request's result
+equals the same request solved alone (wfq_solve_gmres), within the acceptance tolerance
+(alpha relative error 1e-6; both residuals <= 1e-8)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_server_results_same_alone_and_in_the_mix(S):
+    from paper_2103_00438_gb300 import wfq
+    ctx = wfq.Context(0)
+    store = wfq.STORE_FP64 | wfq.STORE_BF16X2
+    geoms = [wfq.Geometry(ctx, S.honeycomb_flake(10), S.carbon_params(1.51), store=store),
+             wfq.Geometry(ctx, S.nanotube(5, 5, 40), S.carbon_params(1.04), store=store),
+             wfq.Geometry(ctx, S.random_cluster(900, seed=4), dict(S.carbon_params(1.2), r0=2.7), store=store)]
+    rng = np.random.default_rng(7)
+    reqs = []
+    for k in range(14):
+        gi = int(rng.integers(0, len(geoms)))
+        nf = int(rng.integers(1, 6))
+        nd = int(rng.integers(1, 4))
+        om = S.ev(np.sort(rng.uniform(0.1, 1.9, size=nf)))
+        dirs = np.eye(3)[:nd]
+        reqs.append((gi, om, dirs))
+    sv = wfq.Server(ctx, nworkers=3, budget_bytes=8 << 30, max_columns=48)
+    ids = [sv.submit(geoms[gi], om, dirs, m=30, rel_tol=1e-8) for gi, om, dirs in reqs]
+    res = [sv.poll(i, wait=True) for i in ids]
+    sv.close()
+    merged = 0
+    for (gi, om, dirs), r in zip(reqs, res):
+        assert r["status"] == "WFQ_OK", r["stats"]
+        assert max(s["rel_residual"] for s in r["stats"]) <= 1e-8
+        ncols = len(om) * len(dirs)
+        merged += r["batch_columns"] > ncols
+        g = geoms[gi]
+        q_alone, st, status = g.solve_gmres(om, dirs, m=30, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED)
+        assert status == "WFQ_OK"
+        a_mix = g.polarizability(r["q"])
+        a_alone = g.polarizability(q_alone)
+        assert np.abs(a_mix - a_alone).max() <= 1e-6 * np.abs(a_alone).max()
+        assert r["latency_s"] >= r["queue_s"] >= 0.0
+    assert merged >= 2, "no request shared a block solve"
+    for g in geoms:
+        g.close()
+    ctx.close()
+
+
+def test_server_rejects_bad_requests(S):
+    from paper_2103_00438_gb300 import wfq
+    ctx = wfq.Context(0)
+    g = wfq.Geometry(ctx, S.honeycomb_flake(4), S.carbon_params(1.51), store=wfq.STORE_BF16X2)
+    sv = wfq.Server(ctx, nworkers=1, budget_bytes=1 << 20, max_columns=8)
+    with pytest.raises(wfq.WfqError) as e:
+        sv.submit(g, [0.0], [[1, 0, 0]])
+    assert e.value.code == -2
+    with pytest.raises(wfq.WfqError) as e:
+        sv.submit(g, S.ev(np.linspace(0.2, 1.0, 5)), np.eye(3))   # 15 columns > 8
+    assert e.value.code == -1
+    sv.close()
+    g.close()
+    ctx.close()
