@@ -49,9 +49,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
-    ap.add_argument("--mode", default=None, choices=["solve", "apply"],
+    ap.add_argument("--mode", default=None, choices=["solve", "apply", "serve"],
                     help="solve: block solves per second (default); apply: operator applies, "
-                         "pair interactions per second (default for disk1m)")
+                         "pair interactions per second (default for disk1m); serve: seeded Poisson "
+                         "request stream through the request server (default for workload serve)")
+    ap.add_argument("--requests", type=int, default=2000, help="serve mode: requests in the stream")
+    ap.add_argument("--workers", type=int, default=3, help="serve mode: server worker streams")
+    ap.add_argument("--load", type=float, default=0.8, help="serve mode: arrival rate / measured capacity")
     return ap.parse_args()
 
 
@@ -240,6 +244,8 @@ def run_ours(args, rank, world, dist):
     import torch
     from paper_2103_00438_gb300 import wfq
 
+    if args.mode == "serve" or args.workload == "serve":
+        return run_serve(args, rank, world, dist)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     wl = workload(args.workload)
@@ -496,6 +502,184 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
         out["e2e"] = {"value": pairs * args.steps * world / te / 1e9, "unit": "Gint/s",
                       "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
     g.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ serving
+
+def run_serve(args, rank, world, dist):
+    """Seeded Poisson stream of (structure, frequencies, directions) requests through the
+    request server (continuous batching, memory admission, worker streams), every request
+    through the public API with host buffers.  The arrival rate is `--load` times the
+    capacity measured on a closed-loop batch of the same stream just before.  Reported:
+    solves/s over the stream, p50/p99 request latency (submit to result in host memory),
+    and the same columns solved one (omega, direction) at a time by plain FP64 GMRES(50)
+    on the same GPU (sampled per structure, extrapolated over the stream's mix)."""
+    import torch
+    from paper_2103_00438_gb300 import structures as S
+    from paper_2103_00438_gb300 import wfq
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    mix = S.serving_mix(args.requests)
+    pool, reqs, gaps = mix["pool"], mix["requests"], mix["gaps"]
+    ctx = wfq.Context(local)
+    store = wfq.STORE_FP64 | wfq.STORE_BF16X2
+    geoms = [wfq.Geometry(ctx, p["xyz"], p["params"], store=store) for p in pool]
+    m, tol, max_iter = args.m, 1e-8, 4000
+    sv = wfq.Server(ctx, nworkers=args.workers, budget_bytes=96 << 30, max_columns=384)
+    ncol = lambda r: len(r[1]) * len(r[2])
+
+    def closed_loop(batch):
+        t0 = time.perf_counter()
+        ids = [sv.submit(geoms[si], om, d, m=m, rel_tol=tol, max_iter=max_iter) for si, om, d in batch]
+        res = [sv.poll(i, wait=True) for i in ids]
+        return res, time.perf_counter() - t0
+
+    # warm-up and capacity: two closed-loop batches drawn from the same seeded stream
+    nwarm = max(args.warmup, 1) * 8
+    rng = np.random.default_rng(20210306)
+    closed_loop([reqs[int(i)] for i in rng.integers(0, len(reqs), size=nwarm)])
+    cal = [reqs[int(i)] for i in rng.integers(0, len(reqs), size=max(len(reqs) // 10, 24))]
+    res_cal, t_cal = closed_loop(cal)
+    capacity = sum(ncol(r) for r in cal) / t_cal                 # solves/s, closed loop
+    mean_cols = float(np.mean([ncol(r) for r in reqs]))
+    rate = args.load * capacity / mean_cols                      # requests/s
+    arrivals = np.cumsum(gaps) / rate
+
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile(True)
+    launches0 = wfq.kernel_launches()
+    ids = [None] * len(reqs)
+    submit_err = []
+
+    def submitter():
+        t0 = time.perf_counter()
+        try:
+            for k, (si, om, d) in enumerate(reqs):
+                dt = arrivals[k] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                ids[k] = sv.submit(geoms[si], om, d, m=m, rel_tol=tol, max_iter=max_iter)
+        except Exception as e:    # reported below; the poll loop stops at the first missing id
+            submit_err.append(repr(e))
+
+    t_start = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    results = []
+    for k in range(len(reqs)):
+        while ids[k] is None and th.is_alive():
+            time.sleep(1e-4)
+        if ids[k] is None:
+            break
+        results.append(sv.poll(ids[k], wait=True))
+    th.join()
+    t_stream = time.perf_counter() - t_start
+    launches = wfq.kernel_launches() - launches0
+    clk = clocks.stop()
+    gemm_n, gemm_ms, gemm_flops = ctx.profile_read(wfq.KT_GEMM_MIXED)
+    ctx.profile(False)
+    sv.close()
+    if submit_err:
+        raise RuntimeError("submit failed: " + submit_err[0])
+
+    ok = [r for r in results if r["status"] == "WFQ_OK"]
+    solves = sum(len(r["stats"]) for r in ok)
+    lat = np.array([r["latency_s"] for r in results])
+    qwait = np.array([r["queue_s"] for r in results])
+    max_res = max(s["rel_residual"] for r in results for s in r["stats"])
+    merged = sum(1 for r, q in zip(results, reqs) if r["batch_columns"] > ncol(q))
+    by_status = {}
+    for r, q in zip(results, reqs):
+        key = "%s/%s" % (pool[q[0]]["name"], r["status"])
+        by_status[key] = by_status.get(key, 0) + 1
+    value = solves / t_stream
+
+    # plain FP64 GMRES(50), one (omega, direction) column at a time, on the same GPU:
+    # two sampled columns per structure, extrapolated over the stream's columns
+    t_plain = {}
+    for si, gm in enumerate(geoms):
+        own = [r for r in reqs if r[0] == si][:2]
+        ts = []
+        for _, om, d in own:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st, status = gm.solve_gmres(om[:1], d[:1], m=50, rel_tol=tol, max_iter=max_iter, prec=wfq.PREC_FP64)
+            ts.append(time.perf_counter() - t0)
+            if status != "WFQ_OK":
+                raise RuntimeError(f"plain FP64 GMRES did not converge on {pool[si]['name']}")
+        t_plain[si] = float(np.mean(ts))
+    plain_time = sum(ncol(r) * t_plain[r[0]] for r in reqs)
+    plain_value = sum(ncol(r) for r in reqs) / plain_time
+
+    # accuracy audit against the FP64 oracle: the first request on each structure of at most
+    # 2,000 atoms, its first column
+    audit = []
+    if not args.no_cpu_baseline:
+        from oracle import build as ob
+        from oracle import oracle as orc
+        ob.build()
+        for si, pdesc in enumerate(pool):
+            if len(pdesc["xyz"]) > 2000:
+                continue
+            k = next(i for i, r in enumerate(reqs) if r[0] == si)
+            xyz, p = pdesc["xyz"], pdesc["params"]
+            csr = orc.kbar_csr(xyz, p)
+            op = orc.Operator.stored(orc.d_matrix(xyz, p["eta"]), csr)
+            R = orc.rhs_csr(xyz, csr, reqs[k][2][0]).astype(complex)
+            q, _ = op.gmres(orc.z_of_omega(reqs[k][1][0], p), R, restart=50, rel_tol=1e-10, max_iter=20000)
+            a_ref = orc.alpha(xyz, q)
+            a_gpu = geoms[si].polarizability(results[k]["q"][:, :1])[0]
+            audit.append(float(np.abs(a_gpu - a_ref).max() / np.abs(a_ref).max()))
+
+    peaks, peak_src = load_peaks()
+    roof = None
+    if gemm_n:
+        achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "gemm_3xbf16 (k_gemm3_tc)", "launches": gemm_n,
+                "avg_ms": gemm_ms / gemm_n,
+                "peak_source": peak_src + " bf16_tflops_sustained (kernel timed inside a long step)"}
+    h2d = sum(r[1].nbytes + r[2].nbytes for r in reqs)
+    d2h = sum(len(pool[r[0]]["xyz"]) * ncol(r) * 16 for r in reqs)
+    out = {"metric": "freq-point solves/s (serving mix)", "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": 1, "warmup": nwarm, "ms_per_step": t_stream * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32+f64", "data": "synthetic",
+           "config": {"workload": "serve: seeded Poisson stream (seed 20210305) of %d requests over %d resident "
+                                  "structures (%s), 1-64 frequencies x 1-3 directions each" %
+                                  (len(reqs), len(pool), ", ".join("%s N=%d" % (p["name"], len(p["xyz"]))
+                                                                   for p in pool)),
+                      "requests": len(reqs), "mean_columns_per_request": mean_cols,
+                      "arrival_rate_req_per_s": rate, "load": args.load,
+                      "capacity_closed_loop_solves_per_s": capacity, "workers": args.workers,
+                      "solver": f"gmres({m})", "rel_tol": tol, "parallelism": f"replicas{world}",
+                      "l2": "resident D planes of all structures (%.1f GB) larger than L2" %
+                            (sum(4.0 * len(p["xyz"]) ** 2 for p in pool) / 1e9)},
+           "latency": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                       "mean_s": float(lat.mean()), "max_s": float(lat.max()),
+                       "queue_p50_s": float(np.percentile(qwait, 50)),
+                       "queue_p99_s": float(np.percentile(qwait, 99))},
+           "accuracy": {"requests_ok": len(ok), "requests": len(results), "max_rel_residual": max_res,
+                        "alpha_rel_err_vs_oracle_sampled": max(audit) if audit else None,
+                        "requests_merged_into_larger_blocks": merged, "by_structure_status": by_status},
+           "plain_fp64_gmres_same_gpu": {"value": plain_value, "unit": "solves/s",
+                                         "sample": "2 columns per structure, one (omega, direction) per "
+                                                   "wfq_solve_gmres call, FP64, GMRES(50), rel. tol 1e-8; "
+                                                   "extrapolated over the stream's columns",
+                                         "seconds_per_column": {pool[s]["name"]: t for s, t in t_plain.items()},
+                                         "served_over_plain": value / plain_value},
+           "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   "includes": "every request through wfq_server_submit/poll with host buffers: the value itself "
+                               "is end to end (structures resident, built before the stream)"}}
+    for gm in geoms:
+        gm.close()
     ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

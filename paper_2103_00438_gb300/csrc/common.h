@@ -226,6 +226,8 @@ struct SolveArgs {
     int refine_every = 0;
     double2 *q = nullptr;           // device, n x ncols
     wfq_stats *stats = nullptr;     // host, ncols (may be null)
+    // Internal (never set through the C ABI): q already holds an initial guess.
+    bool warm = false;
 };
 
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s);

@@ -361,7 +361,9 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
         return cudaErrorInvalidValue;
     const int64_t grid = grid_size(mtiles, num_sms);
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 512;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm3_mf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<uint64_t> smem_set{0};
+    if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+    cudaError_t e = allow_max_smem(k_gemm3_mf, smem_set);
     if (e != cudaSuccess) return e;
     k_gemm3_mf<<<(unsigned)grid, MF_THREADS, smem, s>>>(m_xhi, m_xlo, mp);
     return cudaGetLastError();

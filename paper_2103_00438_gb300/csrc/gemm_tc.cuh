@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 
@@ -400,6 +401,22 @@ inline bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t 
 
 constexpr int kMaxDynSmem = 232448;   // 227 KiB per block
 
+// Raise a kernel's dynamic shared-memory limit to the 227 KiB maximum, once per device.
+// The limit is process-wide state of the function, so it is never lowered to one launch's
+// size: host threads launching different sizes concurrently would otherwise race, and a
+// launch could find the limit below its own request.
+template <class Kernel>
+inline cudaError_t allow_max_smem(Kernel kernel, std::atomic<uint64_t> &devices_done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (devices_done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) devices_done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
 // CTAs of one launch: one per SM when there are at least as many row tiles as SMs
 // (stream-K ranges of >= one tile: a tile is shared by at most two CTAs); otherwise each
 // tile is split in at most two halves, which keeps the result deterministic.
@@ -447,7 +464,9 @@ inline cudaError_t launch_group(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *D
         return cudaErrorInvalidValue;
     const int64_t grid = grid_size(mtiles, num_sms);
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 256;
-    cudaError_t e = cudaFuncSetAttribute(k_gemm3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<uint64_t> smem_set{0};
+    if (smem > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
+    cudaError_t e = allow_max_smem(k_gemm3_tc, smem_set);
     if (e != cudaSuccess) return e;
     k_gemm3_tc<<<(unsigned)grid, NUM_THREADS, smem, s>>>(m_dhi, m_dlo, m_xhi, m_xlo, p);
     return cudaGetLastError();

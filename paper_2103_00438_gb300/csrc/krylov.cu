@@ -399,6 +399,14 @@ __global__ void k_gather(uint32_t total, uint32_t na, int64_t ncol, const int *_
 }
 
 // dst[r][idx[k]] += src[r][k]
+__global__ void k_scatter_set(uint32_t total, uint32_t na, int64_t ncol, const int *__restrict__ idx,
+                              const double2 *__restrict__ src, double2 *__restrict__ dst) {
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const uint32_t r = e / na, k = e % na;
+    dst[(int64_t)r * ncol + idx[k]] = src[e];
+}
+
 __global__ void k_scatter_add(uint32_t total, uint32_t na, int64_t ncol, const int *__restrict__ idx,
                               const double2 *__restrict__ src, double2 *__restrict__ dst) {
     const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -692,8 +700,23 @@ static int finish_stats(const SolveArgs &a, const Common &cm, const std::vector<
 
 // ------------------------------------------------------------------ GMRES
 
+// Per-column outcome of one GMRES run, for the caller that continues it.
+struct GmresOut {
+    std::vector<int> escalate;   // mixed solve: columns whose refinement stagnated
+    std::vector<double> res;     // final relative residual (FP64 true residual)
+    std::vector<int> iters;      // Krylov iterations
+    int cycles = 0;
+};
+
+// A refinement cycle of the mixed solve must shrink a column's FP64 true residual by at
+// least this factor; a column that gains less (its operator error times the conditioning of
+// A - zI is not small) leaves the mixed solve and is finished with FP64 vectors and the
+// double-float D product.
+constexpr double STAGNATION_RATIO = 0.25;
+constexpr int FLOOR_CYCLES = 5;
+
 template <class VT>
-static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
+static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *out) {
     Common cm;
     WFQ_TRY(cm.init(g, a, s));
     const int64_t n = cm.n, cc = cm.cc;
@@ -724,7 +747,7 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         WFQ_TRY(U32.alloc(ctx, n * cc, s));
         WFQ_TRY(scratch.alloc(ctx, mixed_scratch_bytes(g, cc), s));
     }
-    WFQ_CUDA(cudaMemsetAsync(a.q, 0, sizeof(double2) * n * cc, s));
+    if (!a.warm) WFQ_CUDA(cudaMemsetAsync(a.q, 0, sizeof(double2) * n * cc, s));
     const double inner_red = mixed ? 1e-6 : 0.0;
     std::vector<int> act(cc), still;
     for (int64_t c = 0; c < cc; ++c) act[c] = (int)c;
@@ -735,17 +758,48 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         WFQ_TRY(y32.alloc(ctx, n * cc, s));
     }
     int total = 0, cycles = 0;
-    // x0 = 0: the first residual is R itself
     WFQ_TRY(cm.select(act));
-    WFQ_CUDA(cudaMemcpyAsync(cm.ra.ptr, cm.Ba.ptr, sizeof(double2) * n * cc, cudaMemcpyDeviceToDevice, s));
-    WFQ_TRY(cm.colnorm(cm.ra.ptr, cc, cm.rnorm.ptr));
+    if (a.warm) {
+        WFQ_TRY(cm.true_residual(a.q, cc));
+    } else {   // x0 = 0: the first residual is R itself
+        WFQ_CUDA(cudaMemcpyAsync(cm.ra.ptr, cm.Ba.ptr, sizeof(double2) * n * cc, cudaMemcpyDeviceToDevice, s));
+        WFQ_TRY(cm.colnorm(cm.ra.ptr, cc, cm.rnorm.ptr));
+    }
     bool exact = true;   // the current residual block was computed to FP64 accuracy
     std::vector<double2> g_h;
     std::vector<int> jd_h;
+    std::vector<double> prev_exact(cc, -1.0);   // last FP64 relative residual per column
+    std::vector<int> esc, flat_cycles(cc, 0);
 
     for (;;) {
         if (exact) {
             WFQ_TRY(cm.classify(act, a.rel_tol, still));
+            if (mixed && out) {
+                std::vector<int> keep;
+                keep.reserve(still.size());
+                for (int c : still) {
+                    if (prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c])
+                        esc.push_back(c);
+                    else
+                        keep.push_back(c);
+                    prev_exact[c] = cm.res_h[c];
+                }
+                still.swap(keep);
+            } else if (!mixed) {
+                // FP64: a column within 100 x tol whose true residual fell by less than 10% in
+                // each of FLOOR_CYCLES consecutive cycles sits at the rounding floor of its
+                // residual; it stops (not converged) instead of cycling to max_iter.
+                std::vector<int> keep;
+                keep.reserve(still.size());
+                for (int c : still) {
+                    const bool flat = prev_exact[c] >= 0.0 && cm.res_h[c] > 0.9 * prev_exact[c] &&
+                                      cm.res_h[c] < 100.0 * a.rel_tol;
+                    flat_cycles[c] = flat ? flat_cycles[c] + 1 : 0;
+                    prev_exact[c] = cm.res_h[c];
+                    if (flat_cycles[c] < FLOOR_CYCLES) keep.push_back(c);
+                }
+                still.swap(keep);
+            }
             if (still.empty() || total >= a.max_iter) break;
             if (still.size() != act.size()) WFQ_TRY(cm.narrow(act, still));
         } else if (total >= a.max_iter) {
@@ -845,6 +899,13 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
             exact = true;
         }
     }
+    if (out) {
+        std::sort(esc.begin(), esc.end());
+        out->escalate = esc;
+        out->res = cm.res_h;
+        out->iters = iters_h;
+        out->cycles = cycles;
+    }
     return finish_stats(a, cm, iters_h, cycles, {});
 }
 
@@ -860,9 +921,71 @@ size_t solve_footprint(const wfq_geom *g, int64_t cc, int m, int prec) {
     return b;
 }
 
+// Finish the columns a mixed solve gave up on: plain FP64 GMRES(m), warm-started from the
+// mixed iterate; statistics of those columns are merged.  FP64 rather than double-float
+// products: where ||A|| ||x|| / ||R|| is large (low frequencies on large flakes), the
+// double-float product's ~1e-14 relative error already sits near the 1e-8 residual bar.
+static int gmres_escalate(wfq_geom *g, const SolveArgs &a, const GmresOut &o1, cudaStream_t s) {
+    const std::vector<int> &esc = o1.escalate;
+    const int64_t ne = (int64_t)esc.size(), n = g->n, cc = (int64_t)o1.res.size();
+    std::vector<double> om(ne);
+    std::vector<int> dir(ne);
+    for (int64_t k = 0; k < ne; ++k) {
+        const int c = esc[k];
+        om[k] = a.col_omega ? a.col_omega[c] : a.omega[c / a.ndir];
+        dir[k] = a.col_dir ? a.col_dir[c] : c % a.ndir;
+    }
+    DevBuf<double2> q2;
+    DevBuf<int> idx;
+    WFQ_TRY(q2.alloc(g->ctx, n * ne, s));
+    WFQ_TRY(idx.alloc(g->ctx, ne, s));
+    WFQ_CUDA(cudaMemcpyAsync(idx.ptr, esc.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, s));
+    const uint32_t tot = (uint32_t)(n * ne);
+    k_gather<double2, double2><<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)ne, cc, idx.ptr, a.q, q2.ptr); note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    std::vector<wfq_stats> st2(ne);
+    SolveArgs b = a;
+    b.col_omega = om.data();
+    b.col_dir = dir.data();
+    b.ncols = ne;
+    b.q = q2.ptr;
+    b.stats = st2.data();
+    b.prec = WFQ_PREC_FP64;
+    b.warm = true;
+    int used = 0;
+    for (int c : esc) used = std::max(used, o1.iters[c]);
+    b.max_iter = std::max(1, a.max_iter - used);
+    const int rc2 = gmres_impl<double2>(g, b, s, nullptr);
+    if (rc2 != WFQ_OK && rc2 != WFQ_ENOCONV) return rc2;
+    k_scatter_set<<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)ne, cc, idx.ptr, q2.ptr, a.q); note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    WFQ_CUDA(cudaStreamSynchronize(s));   // idx, q2 and om/dir are released on return
+    bool all = true;
+    for (int64_t c = 0; c < cc; ++c) all = all && (o1.res[c] <= a.rel_tol || std::binary_search(esc.begin(), esc.end(), (int)c));
+    for (int64_t k = 0; k < ne; ++k) {
+        all = all && st2[k].status == WFQ_OK;
+        if (a.stats) {
+            wfq_stats &st = a.stats[esc[k]];
+            st.iters += st2[k].iters;
+            st.restarts += st2[k].restarts + 1;
+            st.rel_residual = st2[k].rel_residual;
+            st.rmse = st2[k].rmse;
+            st.status = st2[k].status;
+        }
+    }
+    if (all) {
+        set_error("");   // the first stage's non-convergence message no longer applies
+        return WFQ_OK;
+    }
+    return fail(WFQ_ENOCONV, "iteration limit reached before rel_tol in some column");
+}
+
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
-    if (a.prec == WFQ_PREC_MIXED) return gmres_impl<float2>(g, a, s);
-    return gmres_impl<double2>(g, a, s);
+    if (a.prec != WFQ_PREC_MIXED) return gmres_impl<double2>(g, a, s, nullptr);
+    GmresOut o1;
+    const int rc = gmres_impl<float2>(g, a, s, &o1);
+    if (o1.escalate.empty() || (rc != WFQ_OK && rc != WFQ_ENOCONV)) return rc;
+    return gmres_escalate(g, a, o1, s);
 }
 
 // ------------------------------------------------------------------ QMR
@@ -1025,7 +1148,7 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     for (DevBuf<double> *b : {&tau, &theta, &c2, &target}) WFQ_TRY(b->alloc(ctx, cc, s));
     for (DevBuf<int> *b : {&done, &iters, &brk}) WFQ_TRY(b->alloc(ctx, cc, s));
     if (mixed) WFQ_TRY(scratch.alloc(ctx, mixed_scratch_bytes(g, cc), s));
-    WFQ_CUDA(cudaMemsetAsync(a.q, 0, sizeof(double2) * n * cc, s));
+    if (!a.warm) WFQ_CUDA(cudaMemsetAsync(a.q, 0, sizeof(double2) * n * cc, s));
     const double inner_red = mixed ? 1e-6 : 0.0;
 
     std::vector<int> act(cc), still, iters_h(cc, 0), brk_h(cc, 0), done_h, tmp_i, b_a;

@@ -267,3 +267,39 @@ def workload(name: str) -> dict:
                 "params": carbon_params(1.84),
                 "omega": ev(np.linspace(0.05, 0.20, 16)), "dirs": dirs3[:1]}
     raise KeyError(name)
+
+
+def serving_mix(n_requests: int = 2000, seed: int = 20210305) -> dict:
+    """Seeded serving stream over a resident pool of structures from the paper's three
+    families (honeycomb flakes, armchair (n, n) nanotubes, fcc sodium-like spheres).
+
+    pool      list of dicts: name, xyz (bohr), params, band (eV) -- 1k to 20k atoms
+    requests  list of (structure index, omega (hartree, sorted), dirs (ndir x 3)); each
+              request draws its structure uniformly from the pool, 1-64 frequencies
+              uniform in the family's band and 1-3 field directions (x, then y, then z)
+    gaps      Poisson-process inter-arrival times in units of the mean gap (Exp(1))
+    """
+    a_na = 4.23
+    pool = [
+        {"name": "flake1k", "xyz": honeycomb_flake(13), "params": carbon_params(1.51), "band": (0.05, 2.0)},
+        {"name": "flake5k", "xyz": honeycomb_flake(29), "params": carbon_params(1.51), "band": (0.05, 2.0)},
+        {"name": "flake15k", "xyz": honeycomb_flake(50), "params": carbon_params(1.51), "band": (0.05, 2.0)},
+        {"name": "cnt5_5k", "xyz": nanotube(5, 5, 250), "params": carbon_params(1.04), "band": (0.05, 2.0)},
+        {"name": "cnt10_10k", "xyz": nanotube(10, 10, 250), "params": carbon_params(1.04), "band": (0.05, 2.0)},
+        {"name": "cnt15_20k", "xyz": nanotube(15, 15, 334), "params": carbon_params(1.04), "band": (0.05, 2.0)},
+        {"name": "sphere2k", "xyz": fcc_sphere(a_na, fcc_sphere_radius_for(2000, a_na), 0.05, seed=seed),
+         "params": sodium_params(), "band": (0.9, 1.8)},
+        {"name": "sphere10k", "xyz": fcc_sphere(a_na, fcc_sphere_radius_for(10000, a_na), 0.05, seed=seed + 1),
+         "params": sodium_params(), "band": (0.9, 1.8)},
+    ]
+    rng = np.random.default_rng(seed)
+    dirs3 = np.eye(3)
+    reqs = []
+    for _ in range(n_requests):
+        si = int(rng.integers(0, len(pool)))
+        nf = int(rng.integers(1, 65))
+        nd = int(rng.integers(1, 4))
+        lo, hi = pool[si]["band"]
+        reqs.append((si, ev(np.sort(rng.uniform(lo, hi, size=nf))), dirs3[:nd]))
+    gaps = rng.exponential(1.0, size=n_requests)
+    return {"pool": pool, "requests": reqs, "gaps": gaps}

@@ -112,6 +112,32 @@ def _host_f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _buf(a, dtype, rows, size, out, name):
+    """(array, pointer) of a caller buffer the library reads (out=False) or writes
+    (out=True): C-contiguous, element type `dtype`, `size` elements, first axis `rows`.
+    A numpy input of another type or layout is copied into that form; outputs and torch
+    tensors must already have it (the library would otherwise read or write the wrong
+    elements)."""
+    dtype = np.dtype(dtype)
+    if hasattr(a, "data_ptr"):   # torch tensor
+        import torch
+        want = {np.dtype(np.complex128): torch.complex128, np.dtype(np.complex64): torch.complex64,
+                np.dtype(np.float64): torch.float64}[dtype]
+        if a.dtype != want or a.numel() != size or not a.is_contiguous() or (a.dim() and a.shape[0] != rows):
+            raise ValueError(f"{name}: need a contiguous {want} tensor of {size} elements ({rows} rows); got "
+                             f"{a.dtype} {tuple(a.shape)}, contiguous={a.is_contiguous()}")
+        return a, a.data_ptr()
+    if out:
+        if (not isinstance(a, np.ndarray) or a.dtype != dtype or a.size != size or not a.flags.c_contiguous
+                or not a.flags.writeable or (a.ndim and a.shape[0] != rows)):
+            raise ValueError(f"{name}: need a writable C-contiguous {dtype} array of {size} elements ({rows} rows)")
+        return a, a.ctypes.data
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if arr.size != size or (arr.ndim and arr.shape[0] != rows):
+        raise ValueError(f"{name}: need {size} elements ({rows} rows), got shape {arr.shape}")
+    return arr, arr.ctypes.data
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -189,21 +215,27 @@ class Geometry:
     def apply(self, omega, x, y, prec: int = PREC_FP64, stream=None):
         """y = (A - z(omega_c) I) x; x, y: (n, ncplx) complex128 (FP64) / complex64 (MIXED)."""
         om = _host_f64(np.atleast_1d(omega))
-        _check(_lib.wfq_apply(self.h, len(om), _ptr(om), _ptr(x), _ptr(y), int(prec), _stream_handle(stream)))
+        dt = np.complex64 if prec == PREC_MIXED else np.complex128
+        x, px = _buf(x, dt, self.n, self.n * len(om), False, "x")
+        y, py = _buf(y, dt, self.n, self.n * len(om), True, "y")
+        _check(_lib.wfq_apply(self.h, len(om), _ptr(om), px, py, int(prec), _stream_handle(stream)))
         return y
 
     def apply_mixed_noalloc(self, omega, x, y, stream=None):
         """wfq_apply_mixed_noalloc: the mixed apply with the library's static scratch
         array instead of any allocation; x, y must be device (torch CUDA) complex64."""
         om = _host_f64(np.atleast_1d(omega))
-        _check(_lib.wfq_apply_mixed_noalloc(self.h, len(om), _ptr(om), _ptr(x), _ptr(y), _stream_handle(stream)))
+        x, px = _buf(x, np.complex64, self.n, self.n * len(om), False, "x")
+        y, py = _buf(y, np.complex64, self.n, self.n * len(om), True, "y")
+        _check(_lib.wfq_apply_mixed_noalloc(self.h, len(om), _ptr(om), px, py, _stream_handle(stream)))
         return y
 
     def rhs(self, dirs, E0=1.0, out=None, stream=None):
         d = _host_f64(np.atleast_2d(dirs))
         if out is None:
             out = np.empty((self.n, len(d)), dtype=np.float64)
-        _check(_lib.wfq_rhs(self.h, len(d), _ptr(d), float(E0), _ptr(out), _stream_handle(stream)))
+        out, po = _buf(out, np.float64, self.n, self.n * len(d), True, "out")
+        _check(_lib.wfq_rhs(self.h, len(d), _ptr(d), float(E0), po, _stream_handle(stream)))
         return out
 
     def _solve(self, qmr, omega, dirs, E0, m, rel_tol, max_iter, prec, refine_every, out, stream):
@@ -212,14 +244,15 @@ class Geometry:
         ncols = len(om) * len(d)
         if out is None:
             out = np.empty((self.n, ncols), dtype=np.complex128)
+        out, pq = _buf(out, np.complex128, self.n, self.n * ncols, True, "out")
         stats = (Stats * ncols)()
         if qmr:
             rc = _lib.wfq_solve_qmr(self.h, len(om), _ptr(om), len(d), _ptr(d), float(E0), float(rel_tol),
-                                    int(max_iter), int(prec), int(refine_every), _ptr(out),
+                                    int(max_iter), int(prec), int(refine_every), pq,
                                     ctypes.cast(stats, _P), _stream_handle(stream))
         else:
             rc = _lib.wfq_solve_gmres(self.h, len(om), _ptr(om), len(d), _ptr(d), float(E0), int(m),
-                                      float(rel_tol), int(max_iter), int(prec), _ptr(out),
+                                      float(rel_tol), int(max_iter), int(prec), pq,
                                       ctypes.cast(stats, _P), _stream_handle(stream))
         _check(rc, allow=(-4, -5))
         st = [{"iters": s.iters, "restarts": s.restarts, "refinements": s.refinements,
@@ -238,9 +271,10 @@ class Geometry:
 
     def polarizability(self, q, E0=1.0, stream=None):
         """alpha (ncols, 3) complex128 from q (n, ncols) complex128 (host or device)."""
-        ncols = q.shape[1]
+        ncols = q.shape[1] if q.ndim == 2 else 1
+        q, pq = _buf(q, np.complex128, self.n, self.n * ncols, False, "q")
         out = np.empty((ncols, 3), dtype=np.complex128)
-        _check(_lib.wfq_polarizability(self.h, ncols, _ptr(q), float(E0), _ptr(out), _stream_handle(stream)))
+        _check(_lib.wfq_polarizability(self.h, ncols, pq, float(E0), _ptr(out), _stream_handle(stream)))
         return out
 
 

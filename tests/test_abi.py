@@ -65,3 +65,25 @@ def test_sm103a_objects_built(lib_path):
     assert logs
     text = "".join(open(os.path.join(bdir, f)).read() for f in logs)
     assert "sm_103a" in text
+
+
+def test_binding_buffer_layout_checks():
+    """Caller buffers cross the ABI as plain pointers, so the binding must hand over
+    C-contiguous memory of the right type: inputs are copied into that form, outputs
+    that are not already in it are refused."""
+    import numpy as np
+    from paper_2103_00438_gb300 import wfq
+    q = (np.arange(12.0) + 1j).reshape(4, 3)
+    view = q[:, :1]                      # strided: its pointer would address q's row 0
+    arr, ptr = wfq._buf(view, np.complex128, 4, 4, False, "q")
+    assert arr.flags.c_contiguous and np.array_equal(arr.ravel(), q[:, 0]) and ptr == arr.ctypes.data
+    arr, _ = wfq._buf(q.real, np.complex128, 4, 12, False, "x")     # converted to complex128
+    assert arr.dtype == np.complex128
+    with pytest.raises(ValueError):
+        wfq._buf(np.empty((4, 6), np.complex128)[:, ::2], np.complex128, 4, 12, True, "y")
+    with pytest.raises(ValueError):
+        wfq._buf(np.empty((4, 3), np.complex64), np.complex128, 4, 12, True, "y")
+    with pytest.raises(ValueError):
+        wfq._buf(np.empty((5, 3), np.complex128), np.complex128, 4, 15, True, "y")
+    out = np.empty((4, 3), np.complex128)
+    assert wfq._buf(out, np.complex128, 4, 12, True, "y")[1] == out.ctypes.data
