@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cnt20k")
-    ap.add_argument("--solver", default="gmres", choices=["gmres", "qmr"])
+    ap.add_argument("--solver", default="gmres", choices=["gmres", "qmr", "shifted"])
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -66,7 +66,7 @@ def store_for(name, wfq):
         return wfq.STORE_BF16X2
     if name in ("disk1m", "disk100k"):
         return 0
-    return wfq.STORE_FP64 | wfq.STORE_BF16X2
+    return wfq.STORE_FP64 | wfq.STORE_BF16X2 | wfq.STORE_F32X2
 
 
 # Minimum FP32-pipe instructions to generate one D entry as a bf16 hi/lo pair on the
@@ -265,6 +265,9 @@ def run_ours(args, rank, world, dist):
         if args.solver == "gmres":
             return g.solve_gmres(om, dirs, m=args.m, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED, out=q,
                                  stream=stream)
+        if args.solver == "shifted":
+            return g.solve_gmres_shifted(om, dirs, m_max=0, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED,
+                                         out=q, stream=stream)
         return g.solve_qmr(om, dirs, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED, out=q, stream=stream)
 
     def step():
@@ -300,6 +303,7 @@ def run_ours(args, rank, world, dist):
     sp_n, sp_ms, _ = ctx.profile_read(wfq.KT_SPARSE)
     or_n, or_ms, _ = ctx.profile_read(wfq.KT_ORTHO)
     rs_n, rs_ms, _ = ctx.profile_read(wfq.KT_RESIDUAL)
+    gv_n, gv_ms, gv_bytes = ctx.profile_read(wfq.KT_DGEMV_DF)
     ctx.profile(False)
     ms = max_over_ranks(ms, dist)
 
@@ -315,7 +319,16 @@ def run_ours(args, rank, world, dist):
     # columns converge): 6 N^2 C tensor flops (three bf16 products of 2 N^2 C each).
     peaks, peak_src = load_peaks()
     roof = None
-    if gemm_n:
+    if gv_n and gv_ms >= gemm_ms:
+        # shifted solver: the dominant kernel streams D (FP32 pair planes) once per launch
+        achieved_gbs = gv_bytes / (gv_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+                "frac": achieved_gbs / peak, "traffic": None,
+                "kernel": "k_dgemv_df (double-float D product of the real Arnoldi vectors)", "launches": gv_n,
+                "avg_ms": gv_ms / gv_n, "bytes_per_launch": gv_bytes / gv_n,
+                "peak_source": peak_src + " hbm_gbs (STREAM-style copy)"}
+    elif gemm_n:
         gemm_avg_ms = gemm_ms / gemm_n
         achieved_tflops = gemm_flops / (gemm_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
@@ -330,21 +343,27 @@ def run_ours(args, rank, world, dist):
 
     out = {"metric": "freq-point solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32+f64",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32x2(double-float)+f64" if args.solver == "shifted" else "bf16x3+f32+f64",
            "data": "synthetic",
            "config": {"workload": args.workload, "n_atoms": n, "nfreq": nf, "ndir": nd, "columns": ncols,
-                      "solver": f"{args.solver}({args.m})" if args.solver == "gmres" else "qmr",
-                      "precision": "mixed: 3xBF16 D products, complex64 basis, FP64 refinement",
+                      "solver": {"gmres": f"gmres({args.m})", "qmr": "qmr",
+                                 "shifted": "shifted gmres (one real Arnoldi per direction, all frequencies)"}[args.solver],
+                      "precision": ("double-float D products (FP32 pair planes), FP64 Arnoldi basis and "
+                                    "per-frequency Givens, FP64-accuracy true residual"
+                                    if args.solver == "shifted" else
+                                    "mixed: 3xBF16 D products, complex64 basis, FP64 refinement"),
                       "rel_tol": 1e-8, "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2 (bf16 D planes %.2f GB)" % (4.0 * n * n / 1e9)},
            "accuracy": {"max_rel_residual": max_res, "columns_converged": good_cols,
                         "iters_min_mean_max": [min(iters), float(np.mean(iters)), max(iters)],
                         "status": status_last},
            "kernel_ms_per_step": {"gemm_3xbf16": gemm_ms / args.steps, "dapply_fp64": f64_ms / args.steps,
+                                  "dgemv_df": gv_ms / args.steps,
                                   "sparse": sp_ms / args.steps, "ortho_phase": or_ms / args.steps,
                                   "residual_phase": rs_ms / args.steps},
            "kernel_launches_per_step": {"gemm_3xbf16": gemm_n / args.steps, "dapply_fp64": f64_n / args.steps,
-                                        "sparse": sp_n / args.steps},
+                                        "dgemv_df": gv_n / args.steps, "sparse": sp_n / args.steps},
            "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
 
     # end to end through the C ABI with host buffers: geometry from host coordinates,
@@ -356,8 +375,12 @@ def run_ours(args, rank, world, dist):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ge = wfq.Geometry(ctx, xyz_pin, p, store=store)
-            ge.solve_gmres(om, dirs, m=args.m, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED,
-                           out=q_host.numpy())
+            if args.solver == "shifted":
+                ge.solve_gmres_shifted(om, dirs, m_max=0, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED,
+                                       out=q_host.numpy())
+            else:
+                ge.solve_gmres(om, dirs, m=args.m, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED,
+                               out=q_host.numpy())
             ge.polarizability(q_host.numpy())
             ge.close()
         torch.cuda.synchronize()
@@ -366,7 +389,8 @@ def run_ours(args, rank, world, dist):
         out["e2e"] = {"value": good_cols * args.steps * world / te, "unit": "solves/s",
                       "h2d_bytes_per_step": int(xyz.nbytes + om.nbytes + dirs.nbytes),
                       "d2h_bytes_per_step": int(n * ncols * 16 + ncols * 3 * 16),
-                      "includes": "geometry build (Kbar CSR, FP64 + bf16 D) from host coordinates, solve, alpha"}
+                      "includes": "geometry build (Kbar CSR, D as FP64, bf16 and FP32 pair planes) from host "
+                                  "coordinates, solve, alpha"}
 
     # CPU baseline (oracle, rank 0, N = 1 only) and accuracy audit of sampled columns
     if rank == 0 and world == 1 and not args.no_cpu_baseline and n > ORACLE_STORED_MAX_N:

@@ -79,6 +79,11 @@ typedef struct {
 #define WFQ_STORE_FP64   1u  /* D in FP64, N*N*8 bytes: FP64 applies and residuals */
 #define WFQ_STORE_BF16X2 2u  /* D as two bf16 planes hi + lo (D ~= hi + lo), Np*Np*4 bytes
                                 with Np = N rounded up to 128: the tensor-core path */
+#define WFQ_STORE_F32X2  4u  /* D as two FP32 planes hi + lo (hi = fl32(D), lo = fl32(D - hi):
+                                48 significant bits), N*Nq*8 bytes with Nq = N rounded up to
+                                4: double-float products on the FP32 pipes without FP64
+                                arithmetic (the shifted solver's operator, the refinement
+                                residual) */
 
 /* Arithmetic of an apply / of the inner Krylov iterations. */
 enum {
@@ -130,7 +135,9 @@ enum {
     WFQ_KT_ORTHO = 3,        /* Arnoldi orthogonalisation of one GMRES step (projections,
                                 norm, Givens, scaling) / the vector updates of a QMR step */
     WFQ_KT_RESIDUAL = 4,     /* FP64 true residual of a cycle (gathers, product, norms) */
-    WFQ_KT_COUNT = 5
+    WFQ_KT_DGEMV_DF = 5,     /* shifted GMRES: double-float D product of the real Arnoldi
+                                vectors (one launch per group of <= 4 directions) */
+    WFQ_KT_COUNT = 6
 };
 
 /* enable != 0: reset the counters and start recording; enable == 0: stop. */
@@ -138,7 +145,8 @@ int wfq_profile(wfq_ctx *ctx, int enable);
 
 /* Launches, summed device milliseconds and summed work of kernel class `kind` (WFQ_KT_*).
  * Work: WFQ_KT_GEMM_MIXED -- tensor flops of the three bf16 products, 6 N^2 C per launch
- * (C = real columns of that launch); WFQ_KT_DAPPLY_FP64 -- 2 N^2 C flops; other classes 0.
+ * (C = real columns of that launch); WFQ_KT_DAPPLY_FP64 -- 2 N^2 C flops; WFQ_KT_DGEMV_DF --
+ * bytes of D read (8 N Nq for the FP32 pair planes, 8 N^2 for the FP64 D); others 0.
  * Any out-pointer may be NULL. */
 int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms, double *work);
 
@@ -225,6 +233,26 @@ int wfq_rhs(wfq_geom *g, int ndir, const double *dirs, double E0, double *R, voi
 int wfq_solve_gmres(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
                     const double *dirs, double E0, int m, double rel_tol, int max_iter,
                     int prec, double *q, wfq_stats *stats, void *stream);
+
+/* As wfq_solve_gmres, by shifted GMRES: A = (Kbar - P) D and R are real and do not
+ * depend on omega (Section 2.1), so the Krylov space of A - z(omega) I from R is the
+ * same for every frequency.  One real Arnoldi process per field direction (FP64 basis,
+ * D applied with double-float products) serves all nfreq frequencies; each column's
+ * GMRES iterate (Eq. 24, q0 = 0) comes from its own complex Givens QR of the shared
+ * Hessenberg matrix shifted by z(omega).  One D product of ndir real vectors per
+ * iteration instead of one of 2 * nfreq * ndir.
+ *   m_max: cap on the Arnoldi basis (0 = 600 vectors; memory 8 * N * ndir * (m_max + 1)
+ *          bytes plus 16 * m_max^2 / 2 per column).
+ *   prec: precision of the block GMRES(50) that continues, from their iterate, the
+ *         columns whose FP64 true residual is still above rel_tol at the end (basis cap
+ *         reached, or rounding of the shared process): WFQ_PREC_MIXED or WFQ_PREC_FP64.
+ * Needs a stored D (WFQ_STORE_F32X2, fastest, or WFQ_STORE_FP64), else WFQ_EUNSUPPORTED.
+ * stats: iters = Arnoldi steps the column used plus any continuation's; restarts = 1 +
+ * the continuation's when a column was continued.  Other arguments and results as
+ * wfq_solve_gmres. */
+int wfq_solve_gmres_shifted(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
+                            const double *dirs, double E0, int m_max, double rel_tol,
+                            int max_iter, int prec, double *q, wfq_stats *stats, void *stream);
 
 /* As wfq_solve_gmres, with the J-symmetric QMR-from-BCG method without look-ahead
  * (Section 3; J = D since D A = A^T D, Eq. 18).  The bilinear form u^T D v needs D v,

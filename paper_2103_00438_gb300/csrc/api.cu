@@ -142,7 +142,7 @@ static int galloc(wfq_geom *g, T **p, size_t count) {
 
 static void free_geom(wfq_geom *g) {
     void *ptrs[] = {g->xyz, g->atom64, g->atom32, g->atomdf, g->eta, g->rowptr, g->col,
-                    g->val64, g->val32, g->D64, g->Dhi, g->Dlo};
+                    g->val64, g->val32, g->D64, g->Dhi, g->Dlo, g->Dfh, g->Dfl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -290,7 +290,7 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     *out = nullptr;
     if (n < 1) return fail(WFQ_EINVAL, "n must be >= 1");
     if (!xyz) return fail(WFQ_EINVAL, "xyz is NULL");
-    if (store & ~(WFQ_STORE_FP64 | WFQ_STORE_BF16X2)) return fail(WFQ_EINVAL, "unknown storage flag");
+    if (store & ~(WFQ_STORE_FP64 | WFQ_STORE_BF16X2 | WFQ_STORE_F32X2)) return fail(WFQ_EINVAL, "unknown storage flag");
     WFQ_TRY(check_params(p));
     if (!finite_all(xyz, 3 * n)) return fail(WFQ_EINVAL, "xyz has a non-finite entry");
     std::vector<double> eta_h(n, p->eta);
@@ -312,6 +312,7 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     g->ctx = ctx;
     g->n = n;
     g->npad = round_up(n, kTilePad);
+    g->ldf = round_up(n, 4);
     g->p = *p;
     g->store = store;
     g->nnz = rowptr[n];
@@ -358,6 +359,10 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     if (store & WFQ_STORE_BF16X2) {
         if ((rc = galloc(g, &g->Dhi, (size_t)g->npad * g->npad))) return bail(rc);
         if ((rc = galloc(g, &g->Dlo, (size_t)g->npad * g->npad))) return bail(rc);
+    }
+    if (store & WFQ_STORE_F32X2) {
+        if ((rc = galloc(g, &g->Dfh, (size_t)n * g->ldf))) return bail(rc);
+        if ((rc = galloc(g, &g->Dfl, (size_t)n * g->ldf))) return bail(rc);
     }
     auto up = [&](void *dst, const void *src, size_t bytes) -> int {
         if (bytes == 0) return WFQ_OK;
@@ -455,7 +460,9 @@ int wfq_rhs(wfq_geom *g, int ndir, const double *dirs, double E0, double *R, voi
     return WFQ_OK;
 }
 
-static int solve_common(bool qmr, wfq_geom *g, int64_t nfreq, const double *omega, int ndir, const double *dirs,
+enum Solver { SOLVE_GMRES, SOLVE_QMR, SOLVE_SHIFTED };
+
+static int solve_common(Solver kind, wfq_geom *g, int64_t nfreq, const double *omega, int ndir, const double *dirs,
                         double E0, int m, double rel_tol, int max_iter, int prec, int refine_every, double *q,
                         wfq_stats *stats, void *stream) {
     if (!g || !omega || !dirs || !q) return fail(WFQ_EINVAL, "NULL argument");
@@ -485,7 +492,9 @@ static int solve_common(bool qmr, wfq_geom *g, int64_t nfreq, const double *omeg
     a.refine_every = refine_every;
     a.q = Q.dev;
     a.stats = stats;
-    int rc = qmr ? solve_qmr(g, a, s) : solve_gmres(g, a, s);
+    int rc = kind == SOLVE_QMR ? solve_qmr(g, a, s)
+             : kind == SOLVE_SHIFTED ? solve_gmres_shifted(g, a, s)
+                                     : solve_gmres(g, a, s);
     if (rc != WFQ_OK && rc != WFQ_ENOCONV && rc != WFQ_EBREAKDOWN) return rc;
     WFQ_TRY(Q.out(s));
     WFQ_CUDA(cudaStreamSynchronize(s));
@@ -494,13 +503,21 @@ static int solve_common(bool qmr, wfq_geom *g, int64_t nfreq, const double *omeg
 
 int wfq_solve_gmres(wfq_geom *g, int64_t nfreq, const double *omega, int ndir, const double *dirs, double E0, int m,
                     double rel_tol, int max_iter, int prec, double *q, wfq_stats *stats, void *stream) {
-    return solve_common(false, g, nfreq, omega, ndir, dirs, E0, m, rel_tol, max_iter, prec, 0, q, stats, stream);
+    return solve_common(SOLVE_GMRES, g, nfreq, omega, ndir, dirs, E0, m, rel_tol, max_iter, prec, 0, q, stats,
+                        stream);
+}
+
+int wfq_solve_gmres_shifted(wfq_geom *g, int64_t nfreq, const double *omega, int ndir, const double *dirs,
+                            double E0, int m_max, double rel_tol, int max_iter, int prec, double *q,
+                            wfq_stats *stats, void *stream) {
+    return solve_common(SOLVE_SHIFTED, g, nfreq, omega, ndir, dirs, E0, m_max, rel_tol, max_iter, prec, 0, q, stats,
+                        stream);
 }
 
 int wfq_solve_qmr(wfq_geom *g, int64_t nfreq, const double *omega, int ndir, const double *dirs, double E0,
                   double rel_tol, int max_iter, int prec, int refine_every, double *q, wfq_stats *stats,
                   void *stream) {
-    return solve_common(true, g, nfreq, omega, ndir, dirs, E0, 0, rel_tol, max_iter, prec, refine_every, q, stats,
+    return solve_common(SOLVE_QMR, g, nfreq, omega, ndir, dirs, E0, 0, rel_tol, max_iter, prec, refine_every, q, stats,
                         stream);
 }
 

@@ -3,6 +3,7 @@
 //   y = Kbar u - P u - z x   (sparse neighbour term of Eq. 16-17 plus the shift of Eq. 14)
 // Block vectors are atom-major: (atom i, complex column c) at i * cc + c.
 #include "common.h"
+#include "dfloat.cuh"
 
 namespace wfq {
 
@@ -191,33 +192,15 @@ __global__ void __launch_bounds__(256) k_dotf(int64_t n, int64_t C, const atom64
 
 // ------------------------------------------------------------------ double-float stored D
 
-// U[n x C] = D[n x n] X[n x C] with every FP64 operand split into a pair of floats
-// (hi = fp32(v), lo = fp32(v - hi): 48 significant bits) and every product accumulated
-// as an unevaluated float sum: the exact product hi*hi (its rounding error recovered with
-// an FMA) plus the cross terms hi*lo + lo*hi, added with Knuth's two-sum so that the
-// running sum keeps ~48 bits.  The dropped lo*lo term and the cross-term roundings are
-// ~2^-48 relative.  This runs on the FP32 pipes, which GB300 has far more of than FP64.
-__device__ __forceinline__ void df_split(double v, float &h, float &l) {
-    h = (float)v;
-    l = (float)(v - (double)h);
-}
+// U[n x C] = D[n x n] X[n x C] with double-float products (df_mac): every FP64 operand
+// split into a float pair (hi = fp32(v), lo = fp32(v - hi): 48 significant bits).  This
+// runs on the FP32 pipes, which GB300 has far more of than FP64.  PL: D comes from the
+// stored FP32 pair planes (no FP64 arithmetic at all); else it is split from the FP64 D.
 
-// The error-free steps use explicit round-to-nearest intrinsics so that the compiler
-// cannot contract them into FMAs (which would break the two-sum identity).
-__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &sh, float &sl) {
-    const float p = __fmul_rn(ah, bh);
-    float e = fmaf(ah, bh, -p);           // exact rounding error of p
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    const float s = __fadd_rn(sh, p);
-    const float v = __fsub_rn(s, sh);
-    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, v)), __fsub_rn(p, v));   // sh + p - s exactly
-    sh = s;
-    sl += t + e;
-}
-
+template <bool PL>
 __global__ void __launch_bounds__(256) k_dgemm_df(int64_t n, int64_t C, const double *__restrict__ D,
-                                                  const double *__restrict__ X, double *__restrict__ U) {
+                                                  const float *__restrict__ Fh, const float *__restrict__ Fl,
+                                                  int64_t ldf, const double *__restrict__ X, double *__restrict__ U) {
     __shared__ float Ah[16][64], Al[16][64], Bh[16][64], Bl[16][64];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
@@ -228,7 +211,13 @@ __global__ void __launch_bounds__(256) k_dgemm_df(int64_t n, int64_t C, const do
             const int e = tid + l * 256;
             const int r = e >> 4, kk = e & 15;
             const int64_t gi = m0 + r, gk = k0 + kk;
-            df_split((gi < n && gk < n) ? D[gi * n + gk] : 0.0, Ah[kk][r], Al[kk][r]);
+            if (PL) {
+                const bool in = gi < n && gk < n;
+                Ah[kk][r] = in ? Fh[gi * ldf + gk] : 0.f;
+                Al[kk][r] = in ? Fl[gi * ldf + gk] : 0.f;
+            } else {
+                df_split((gi < n && gk < n) ? D[gi * n + gk] : 0.0, Ah[kk][r], Al[kk][r]);
+            }
             const int kb = e >> 6, cb = e & 63;
             const int64_t bk = k0 + kb, bc = n0 + cb;
             df_split((bk < n && bc < C) ? X[bk * C + bc] : 0.0, Bh[kb][cb], Bl[kb][cb]);
@@ -387,7 +376,7 @@ __global__ void __launch_bounds__(256) k_dotf_df(int64_t n, int64_t C, const flo
 }
 
 int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
-    if (!g->D64) {
+    if (!g->D64 && !g->Dfh) {
         // matrix-free double-float product
         const int64_t n = g->n, C = 2 * cc;
         if (C <= 2) return d_apply_fp64(g, cc, X, U, s);
@@ -407,11 +396,17 @@ int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cuda
         return WFQ_OK;
     }
     const int64_t n = g->n, C = 2 * cc;
-    if (C <= 8) return d_apply_fp64(g, cc, X, U, s);   // few columns: memory bound, FP64 GEMV
+    if (C <= 8 && g->D64) return d_apply_fp64(g, cc, X, U, s);   // few columns: memory bound, FP64 GEMV
     KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);
     dim3 grid((unsigned)((C + 63) / 64), (unsigned)((n + 63) / 64));
     if (grid.y > 65535u) return fail(WFQ_EUNSUPPORTED, "double-float apply: too many rows");
-    k_dgemm_df<<<grid, 256, 0, s>>>(n, C, g->D64, reinterpret_cast<const double *>(X), reinterpret_cast<double *>(U)); note_launch();
+    const double *x = reinterpret_cast<const double *>(X);
+    double *u = reinterpret_cast<double *>(U);
+    if (g->Dfh)
+        k_dgemm_df<true><<<grid, 256, 0, s>>>(n, C, nullptr, g->Dfh, g->Dfl, g->ldf, x, u);
+    else
+        k_dgemm_df<false><<<grid, 256, 0, s>>>(n, C, g->D64, nullptr, nullptr, 0, x, u);
+    note_launch();
     WFQ_CUDA(cudaGetLastError());
     return WFQ_OK;
 }

@@ -114,6 +114,9 @@ struct wfq_geom {
     double *D64 = nullptr;      // n x n row-major (ld = n)
     __nv_bfloat16 *Dhi = nullptr;  // npad x npad row-major
     __nv_bfloat16 *Dlo = nullptr;
+    float *Dfh = nullptr;       // n x ldf row-major: fl32(D_ij) (zero for j >= n)
+    float *Dfl = nullptr;       // n x ldf row-major: fl32(D_ij - Dfh_ij)
+    int64_t ldf = 0;            // n rounded up to 4 (16-byte rows)
 };
 
 namespace wfq {
@@ -232,6 +235,13 @@ struct SolveArgs {
 
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
 int solve_qmr(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
+// Shifted GMRES (one real Arnoldi per direction for all frequencies); a.m caps the basis.
+int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
+// FP64 true residual of every column of a (iterate in a.q); columns above a.rel_tol continue
+// in block GMRES(m) at a.prec.  iters: Krylov steps already spent per column.  dq: D a.q
+// (n x ncols) when the caller has it, else null (computed with double-float products).
+int finish_columns(wfq_geom *g, const SolveArgs &a, const std::vector<int> &iters, int m, const double2 *dq,
+                   cudaStream_t s);
 
 // Device bytes a block solve of `cc` columns allocates (Krylov basis, FP64 blocks, scratch).
 size_t solve_footprint(const wfq_geom *g, int64_t cc, int m, int prec);

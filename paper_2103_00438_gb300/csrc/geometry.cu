@@ -128,18 +128,24 @@ __device__ __forceinline__ double d_entry64(atom64_t a, atom64_t b, double eta_i
     return erf(r / sqrt(s2)) / r;
 }
 
-// One thread per (i, j) with j fastest; writes the FP64 D and / or the bf16 hi/lo
-// planes (hi = bf16(D), lo = bf16(D - hi), zero outside n x n).
+// One thread per (i, j) with j fastest; writes the FP64 D, the bf16 hi/lo planes
+// (hi = bf16(D), lo = bf16(D - hi), zero outside n x n) and / or the FP32 hi/lo planes
+// (fh = fl32(D), fl = fl32(D - fh), rows of ldf >= n entries, zero for j >= n).
 __global__ void k_build_d(const atom64_t *__restrict__ atom, const double *__restrict__ eta,
-                          int64_t n, int64_t npad, double *__restrict__ D64,
-                          __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+                          int64_t n, int64_t npad, int64_t lim, double *__restrict__ D64,
+                          __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+                          int64_t ldf, float *__restrict__ fh, float *__restrict__ fl) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-    int64_t lim = hi ? npad : n;
     if (i >= lim || j >= lim) return;
     double v = 0.0;
     if (i < n && j < n) v = d_entry64(atom[i], atom[j], eta[i], i == j);
     if (D64 && i < n && j < n) D64[i * n + j] = v;
+    if (fh && i < n && j < ldf) {
+        const float h = (float)v;
+        fh[i * ldf + j] = h;
+        fl[i * ldf + j] = (float)(v - (double)h);
+    }
     if (hi) {
         __nv_bfloat16 h = __double2bfloat16(v);
         __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
@@ -149,12 +155,13 @@ __global__ void k_build_d(const atom64_t *__restrict__ atom, const double *__res
 }
 
 int launch_build_d(const wfq_geom *g, cudaStream_t s) {
-    if (!g->D64 && !g->Dhi) return WFQ_OK;
-    int64_t lim = g->Dhi ? g->npad : g->n;
+    if (!g->D64 && !g->Dhi && !g->Dfh) return WFQ_OK;
+    const int64_t lim = g->Dhi ? g->npad : (g->Dfh ? g->ldf : g->n);   // ldf <= npad
     dim3 block(64, 4);
     dim3 grid((unsigned)((lim + 63) / 64), (unsigned)((lim + 3) / 4));
     if (grid.y > 65535u) return fail(WFQ_EUNSUPPORTED, "stored D with more than 262140 rows");
-    k_build_d<<<grid, block, 0, s>>>(g->atom64, g->eta, g->n, g->npad, g->D64, g->Dhi, g->Dlo); note_launch();
+    k_build_d<<<grid, block, 0, s>>>(g->atom64, g->eta, g->n, g->npad, lim, g->D64, g->Dhi, g->Dlo, g->ldf, g->Dfh,
+                                     g->Dfl); note_launch();
     WFQ_CUDA(cudaGetLastError());
     return WFQ_OK;
 }

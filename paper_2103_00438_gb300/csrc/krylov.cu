@@ -604,6 +604,17 @@ struct Common {
         return colnorm(ra.ptr, na, rnorm.ptr);
     }
 
+    // As true_residual for all cc columns in order (after select of 0..cc-1), with the
+    // product D x supplied (dx, n x cc) instead of computed here.
+    int residual_given_dx(const double2 *x, const double2 *dx) {
+        KScope ks(g->ctx, WFQ_KT_RESIDUAL, s);
+        const uint32_t tot = (uint32_t)(n * cc);
+        WFQ_TRY(sparse_shift_fp64(g, cc, dx, x, za.ptr, Ya.ptr, s));
+        k_residual<<<nblocks(tot), 256, 0, s>>>(tot, Ba.ptr, Ya.ptr, ra.ptr); note_launch();
+        WFQ_CUDA(cudaGetLastError());
+        return colnorm(ra.ptr, cc, rnorm.ptr);
+    }
+
     // Narrow the active set from `act` to `keep` (a subset, same order): the residual
     // block ra and its norms are gathered from the wider block (no new FP64 product),
     // then B, z and ||B|| are re-gathered for the new list.
@@ -708,11 +719,12 @@ struct GmresOut {
     int cycles = 0;
 };
 
-// A refinement cycle of the mixed solve must shrink a column's FP64 true residual by at
-// least this factor; a column that gains less (its operator error times the conditioning of
-// A - zI is not small) leaves the mixed solve and is finished with FP64 vectors and the
-// double-float D product.
-constexpr double STAGNATION_RATIO = 0.25;
+// A column of the mixed solve whose FP64 true residual shrank by less than this factor in
+// each of STAGNATION_CYCLES consecutive refinement cycles (its operator error times the
+// conditioning of A - zI is not small, or its residual sits at the rounding floor of the
+// double-float residual) leaves the mixed solve and is finished in plain FP64.
+constexpr double STAGNATION_RATIO = 0.5;
+constexpr int STAGNATION_CYCLES = 2;
 constexpr int FLOOR_CYCLES = 5;
 
 template <class VT>
@@ -778,11 +790,13 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
                 std::vector<int> keep;
                 keep.reserve(still.size());
                 for (int c : still) {
-                    if (prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c])
+                    const bool slow = prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c];
+                    flat_cycles[c] = slow ? flat_cycles[c] + 1 : 0;
+                    prev_exact[c] = cm.res_h[c];
+                    if (flat_cycles[c] >= STAGNATION_CYCLES)
                         esc.push_back(c);
                     else
                         keep.push_back(c);
-                    prev_exact[c] = cm.res_h[c];
                 }
                 still.swap(keep);
             } else if (!mixed) {
@@ -921,17 +935,21 @@ size_t solve_footprint(const wfq_geom *g, int64_t cc, int m, int prec) {
     return b;
 }
 
-// Finish the columns a mixed solve gave up on: plain FP64 GMRES(m), warm-started from the
-// mixed iterate; statistics of those columns are merged.  FP64 rather than double-float
-// products: where ||A|| ||x|| / ||R|| is large (low frequencies on large flakes), the
-// double-float product's ~1e-14 relative error already sits near the 1e-8 residual bar.
-static int gmres_escalate(wfq_geom *g, const SolveArgs &a, const GmresOut &o1, cudaStream_t s) {
-    const std::vector<int> &esc = o1.escalate;
-    const int64_t ne = (int64_t)esc.size(), n = g->n, cc = (int64_t)o1.res.size();
+// Continue the columns `cols` of a solve from their iterate in a.q: block GMRES(m) at
+// precision `prec` (mixed continuations that stall finish in FP64), warm-started; their q
+// columns and statistics are replaced.  `res` / `iters`: relative residual and Krylov
+// steps so far of every column (the others keep their state).
+static int continue_columns(wfq_geom *g, const SolveArgs &a, const std::vector<int> &cols,
+                            const std::vector<double> &res, const std::vector<int> &iters, int prec, int m,
+                            cudaStream_t s) {
+    const int64_t ne = (int64_t)cols.size(), n = g->n, cc = (int64_t)res.size();
+    int used = 0;
+    for (int c : cols) used = std::max(used, iters[c]);
+    if (a.max_iter - used < 1) return fail(WFQ_ENOCONV, "iteration limit reached before rel_tol in some column");
     std::vector<double> om(ne);
     std::vector<int> dir(ne);
     for (int64_t k = 0; k < ne; ++k) {
-        const int c = esc[k];
+        const int c = cols[k];
         om[k] = a.col_omega ? a.col_omega[c] : a.omega[c / a.ndir];
         dir[k] = a.col_dir ? a.col_dir[c] : c % a.ndir;
     }
@@ -939,7 +957,7 @@ static int gmres_escalate(wfq_geom *g, const SolveArgs &a, const GmresOut &o1, c
     DevBuf<int> idx;
     WFQ_TRY(q2.alloc(g->ctx, n * ne, s));
     WFQ_TRY(idx.alloc(g->ctx, ne, s));
-    WFQ_CUDA(cudaMemcpyAsync(idx.ptr, esc.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, s));
+    WFQ_CUDA(cudaMemcpyAsync(idx.ptr, cols.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, s));
     const uint32_t tot = (uint32_t)(n * ne);
     k_gather<double2, double2><<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)ne, cc, idx.ptr, a.q, q2.ptr); note_launch();
     WFQ_CUDA(cudaGetLastError());
@@ -950,34 +968,63 @@ static int gmres_escalate(wfq_geom *g, const SolveArgs &a, const GmresOut &o1, c
     b.ncols = ne;
     b.q = q2.ptr;
     b.stats = st2.data();
-    b.prec = WFQ_PREC_FP64;
+    b.prec = prec;
+    b.m = m;
     b.warm = true;
-    int used = 0;
-    for (int c : esc) used = std::max(used, o1.iters[c]);
-    b.max_iter = std::max(1, a.max_iter - used);
-    const int rc2 = gmres_impl<double2>(g, b, s, nullptr);
+    b.max_iter = a.max_iter - used;
+    const int rc2 = solve_gmres(g, b, s);
     if (rc2 != WFQ_OK && rc2 != WFQ_ENOCONV) return rc2;
     k_scatter_set<<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)ne, cc, idx.ptr, q2.ptr, a.q); note_launch();
     WFQ_CUDA(cudaGetLastError());
     WFQ_CUDA(cudaStreamSynchronize(s));   // idx, q2 and om/dir are released on return
+    std::vector<char> cont(cc, 0);
+    for (int c : cols) cont[c] = 1;
     bool all = true;
-    for (int64_t c = 0; c < cc; ++c) all = all && (o1.res[c] <= a.rel_tol || std::binary_search(esc.begin(), esc.end(), (int)c));
+    for (int64_t c = 0; c < cc; ++c) all = all && (cont[c] || res[c] <= a.rel_tol);
     for (int64_t k = 0; k < ne; ++k) {
         all = all && st2[k].status == WFQ_OK;
         if (a.stats) {
-            wfq_stats &st = a.stats[esc[k]];
-            st.iters += st2[k].iters;
+            wfq_stats &st = a.stats[cols[k]];
+            st.iters = iters[cols[k]] + st2[k].iters;
             st.restarts += st2[k].restarts + 1;
+            st.refinements += st2[k].refinements;
             st.rel_residual = st2[k].rel_residual;
             st.rmse = st2[k].rmse;
             st.status = st2[k].status;
         }
     }
     if (all) {
-        set_error("");   // the first stage's non-convergence message no longer applies
+        set_error("");   // an earlier stage's non-convergence message no longer applies
         return WFQ_OK;
     }
     return fail(WFQ_ENOCONV, "iteration limit reached before rel_tol in some column");
+}
+
+int finish_columns(wfq_geom *g, const SolveArgs &a, const std::vector<int> &iters, int m, const double2 *dq,
+                   cudaStream_t s) {
+    Common cm;
+    WFQ_TRY(cm.init(g, a, s));
+    cm.residual_df = true;
+    std::vector<int> act(cm.cc), still;
+    for (int64_t c = 0; c < cm.cc; ++c) act[c] = (int)c;
+    WFQ_TRY(cm.select(act));
+    if (dq)
+        WFQ_TRY(cm.residual_given_dx(a.q, dq));
+    else
+        WFQ_TRY(cm.true_residual(a.q, cm.cc));
+    WFQ_TRY(cm.classify(act, a.rel_tol, still));
+    if (a.stats)
+        for (int64_t c = 0; c < cm.cc; ++c) {
+            wfq_stats &st = a.stats[c];
+            st.iters = iters[c];
+            st.restarts = 0;
+            st.refinements = 0;
+            st.rel_residual = cm.res_h[c];
+            st.rmse = cm.res_h[c] * cm.bn_h[c] / std::sqrt((double)cm.n);
+            st.status = cm.res_h[c] <= a.rel_tol ? WFQ_OK : WFQ_ENOCONV;
+        }
+    if (still.empty()) return WFQ_OK;
+    return continue_columns(g, a, still, cm.res_h, iters, a.prec, m, s);
 }
 
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
@@ -985,7 +1032,10 @@ int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     GmresOut o1;
     const int rc = gmres_impl<float2>(g, a, s, &o1);
     if (o1.escalate.empty() || (rc != WFQ_OK && rc != WFQ_ENOCONV)) return rc;
-    return gmres_escalate(g, a, o1, s);
+    // the columns whose mixed refinement stalled finish in plain FP64 from the mixed
+    // iterate: where ||A|| ||x|| / ||R|| is large (low frequencies on large flakes) the
+    // double-float residual's ~1e-14 relative error already sits near the 1e-8 bar
+    return continue_columns(g, a, o1.escalate, o1.res, o1.iters, WFQ_PREC_FP64, a.m, s);
 }
 
 // ------------------------------------------------------------------ QMR

@@ -1,0 +1,581 @@
+// Shifted GMRES: one real Arnoldi process per field direction serves every frequency.
+//
+// A = (Kbar - P) D and the right-hand sides R_k are real and do not depend on omega
+// (Section 2.1, Eq. 13-14); only the shift z(omega) of Eq. 12 does.  Hence the Krylov
+// space K_j(A - z I, R_k) equals K_j(A, R_k) for every z, and one Arnoldi process on A
+// (Eq. 24's basis, started from R_k, real arithmetic) gives for all shifts at once
+//
+//     A V_j = V_{j+1} Hbar_j    =>    (A - z I) V_j = V_{j+1} (Hbar_j - z Ibar_j),
+//
+// with Ibar_j the (j+1) x j identity.  The GMRES iterate of column (omega, k) from x0 = 0
+// is x = V_j y with y minimising || ||R_k|| e1 - (Hbar_j - z Ibar_j) y ||, which each
+// column solves by its own complex Givens QR of the shared real Hbar_j.  One D product of
+// the ndir real Arnoldi vectors per iteration therefore serves all nfreq x ndir columns.
+//
+// Precision: the Arnoldi vectors, Hbar and the rotations are FP64; D is applied with
+// double-float products (~2^-48 relative) on the FP32 pipes, from the stored FP32 pair
+// planes (or split from the FP64 D).  Every column's true residual R - (A - zI) q is
+// measured at the end in FP64 from q = sum_k v_k y_k and D q = sum_k (D v_k) y_k, the D
+// products of the Arnoldi vectors kept from the iteration (D is linear, so this is D q up
+// to the rounding of the double-float products; neither Hbar nor the orthogonality of the
+// basis enters).  Columns above the tolerance (the basis reached its cap, or rounding of
+// the shared process) continue from their iterate in the block GMRES(m) solver.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.h"
+#include "dfloat.cuh"
+
+namespace wfq {
+namespace {
+
+inline unsigned nblk(int64_t total, int t = 256) { return (unsigned)((total + t - 1) / t); }
+
+__device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 c_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 c_scale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 c_conjmul(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double c_abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double2 c_div(double2 a, double2 b) {
+    const double d = c_abs2(b);
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// ------------------------------------------------------------------ operator: A v (real)
+
+// x -> float pairs (hi = fp32(x), lo = fp32(x - hi))
+__global__ void k_split_real(int64_t total, const double *__restrict__ x, float *__restrict__ xh,
+                             float *__restrict__ xl) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    df_split(x[e], xh[e], xl[e]);
+}
+
+constexpr int GV_ROWS = 2;       // rows per warp
+constexpr int GV_TB = 4;         // 128-column steps whose D loads are issued together
+constexpr int GV_WARPS = 8;      // warps per block
+constexpr int GV_CHUNK = 1024;   // x entries staged in shared memory per step
+
+// U[d][i] = sum_j D_ij x[d][j] for C real vectors (direction-major, length n), with
+// double-float products.  Each warp owns GV_ROWS rows and reads them with 16-byte loads
+// (four consecutive j per lane), GV_TB steps of 128 columns at a time so that 2 * GV_ROWS *
+// GV_TB independent loads per lane are in flight before any is used; x is staged per
+// chunk in shared memory as separate hi / lo planes so that a quarter-warp's 16-byte reads
+// are conflict-free.  PL: D from the FP32 pair planes (row pitch ld, a multiple of 4, zero
+// beyond n); else split from the FP64 D.  Entries past n contribute zero (x is zero there).
+template <int C, bool PL>
+__global__ void __launch_bounds__(GV_WARPS * 32) k_dgemv_df(int64_t n, int64_t ld, const float *__restrict__ Fh,
+                                                            const float *__restrict__ Fl,
+                                                            const double *__restrict__ D64,
+                                                            const float *__restrict__ xh,
+                                                            const float *__restrict__ xl, double *__restrict__ U) {
+    __shared__ __align__(16) float sxh[C][GV_CHUNK];
+    __shared__ __align__(16) float sxl[C][GV_CHUNK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = ((int64_t)blockIdx.x * GV_WARPS + warp) * GV_ROWS;
+    float sh[GV_ROWS][C], sl[GV_ROWS][C];
+#pragma unroll
+    for (int r = 0; r < GV_ROWS; ++r)
+#pragma unroll
+        for (int d = 0; d < C; ++d) sh[r][d] = sl[r][d] = 0.f;
+
+    for (int64_t j0 = 0; j0 < n; j0 += GV_CHUNK) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < C * GV_CHUNK; t += GV_WARPS * 32) {
+            const int d = t / GV_CHUNK, jj = t - d * GV_CHUNK;
+            const int64_t j = j0 + jj;
+            sxh[d][jj] = j < n ? xh[(int64_t)d * n + j] : 0.f;
+            sxl[d][jj] = j < n ? xl[(int64_t)d * n + j] : 0.f;
+        }
+        __syncthreads();
+        const int64_t trem = (n - j0 + 127) / 128;
+        const int tend = trem < GV_CHUNK / 128 ? (int)trem : GV_CHUNK / 128;
+        for (int t0 = 0; t0 < tend; t0 += GV_TB) {
+            float4 dh[GV_TB][GV_ROWS], dl[GV_TB][GV_ROWS];
+#pragma unroll
+            for (int t = 0; t < GV_TB; ++t) {
+                const int64_t j = j0 + (t0 + t) * 128 + lane * 4;
+#pragma unroll
+                for (int r = 0; r < GV_ROWS; ++r) {
+                    const int64_t i = row0 + r;
+                    if (i >= n || j >= n) {
+                        dh[t][r] = dl[t][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else if (PL) {
+                        dh[t][r] = __ldg(reinterpret_cast<const float4 *>(Fh + i * ld + j));
+                        dl[t][r] = __ldg(reinterpret_cast<const float4 *>(Fl + i * ld + j));
+                    } else {
+                        const double *row = D64 + i * n;
+                        float h[4], l[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) df_split(j + e < n ? __ldg(row + j + e) : 0.0, h[e], l[e]);
+                        dh[t][r] = make_float4(h[0], h[1], h[2], h[3]);
+                        dl[t][r] = make_float4(l[0], l[1], l[2], l[3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < GV_TB; ++t) {
+                const int jl = (t0 + t) * 128 + lane * 4;
+#pragma unroll
+                for (int d = 0; d < C; ++d) {
+                    const float4 xh4 = *reinterpret_cast<const float4 *>(&sxh[d][jl]);
+                    const float4 xl4 = *reinterpret_cast<const float4 *>(&sxl[d][jl]);
+#pragma unroll
+                    for (int r = 0; r < GV_ROWS; ++r) {
+                        df_mac(dh[t][r].x, dl[t][r].x, xh4.x, xl4.x, sh[r][d], sl[r][d]);
+                        df_mac(dh[t][r].y, dl[t][r].y, xh4.y, xl4.y, sh[r][d], sl[r][d]);
+                        df_mac(dh[t][r].z, dl[t][r].z, xh4.z, xl4.z, sh[r][d], sl[r][d]);
+                        df_mac(dh[t][r].w, dl[t][r].w, xh4.w, xl4.w, sh[r][d], sl[r][d]);
+                    }
+                }
+            }
+        }
+    }
+    // warp sums in double-float, fixed butterfly order
+#pragma unroll
+    for (int r = 0; r < GV_ROWS; ++r)
+#pragma unroll
+        for (int d = 0; d < C; ++d)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh[r][d], off);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl[r][d], off);
+                df_add(sh[r][d], sl[r][d], oh, ol);
+            }
+    if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < GV_ROWS; ++r) {
+            const int64_t i = row0 + r;
+            if (i < n)
+#pragma unroll
+                for (int d = 0; d < C; ++d) U[(int64_t)d * n + i] = (double)sh[r][d] + (double)sl[r][d];
+        }
+    }
+}
+
+// W[d][i] = sum_p Kbar_ip (U[d][j_p] - U[d][i]) = ((Kbar - P) U)_i  (Eq. 16-17), FP64.
+__global__ void k_sparse_real(int64_t n, int C, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                              const double *__restrict__ val, const double *__restrict__ U, double *__restrict__ W) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
+    for (int d = 0; d < C; ++d) {
+        const double *u = U + (int64_t)d * n;
+        const double ui = u[i];
+        double acc = 0.0;
+        for (int64_t p = p0; p < p1; ++p) acc += val[p] * (u[col[p]] - ui);
+        W[(int64_t)d * n + i] = acc;
+    }
+}
+
+// W[d][i] = R[i * C + d]   (atom-major right-hand sides -> direction-major vectors)
+__global__ void k_take_rhs(int64_t n, int C, const double *__restrict__ R, double *__restrict__ W) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * C) return;
+    const int64_t d = e / n, i = e - d * n;
+    W[e] = R[i * C + d];
+}
+
+// ------------------------------------------------------------------ Arnoldi (CGS2, FP64)
+
+constexpr int KV = 8;   // basis vectors per dot-product block
+
+// partial[(rb * nv + k) * C + d] = sum over the rows of block rb of V_k[d][i] w[d][i]
+// for k < nv (vectors V + k * vstride), d = blockIdx.z.  Fixed-order reductions.
+__global__ void __launch_bounds__(256) k_rdot_part(int64_t n, int C, int nv, const double *__restrict__ V,
+                                                   int64_t vstride, const double *__restrict__ w, int64_t rpb,
+                                                   double *__restrict__ partial) {
+    __shared__ double red[8][KV];
+    const int rb = blockIdx.x, d = blockIdx.z, k0 = blockIdx.y * KV;
+    const int kn = min(KV, nv - k0);
+    const int64_t r0 = (int64_t)rb * rpb, r1 = min(n, r0 + rpb);
+    double acc[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) acc[k] = 0.0;
+    const double *wd = w + (int64_t)d * n;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += 256) {
+        const double wi = wd[i];
+#pragma unroll
+        for (int k = 0; k < KV; ++k)
+            if (k < kn) acc[k] += V[(int64_t)(k0 + k) * vstride + (int64_t)d * n + i] * wi;
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[wp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kn) {
+        double s = 0.0;
+        for (int q = 0; q < 8; ++q) s += red[q][threadIdx.x];
+        partial[((int64_t)rb * nv + k0 + threadIdx.x) * C + d] = s;
+    }
+}
+
+enum { RF_SET = 0, RF_ADD = 1, RF_NORM = 2 };
+
+// One warp per output (k, d): s = sum_rb partial (fixed order).
+//   RF_SET : H[d][j][k] = s, coef[k * C + d] = s
+//   RF_ADD : H[d][j][k] += s, coef[k * C + d] = s
+//   RF_NORM: H[d][j][j + 1] = sqrt(s), hn[d] = sqrt(s)   (nv = 1)
+__global__ void k_rdot_fin(int nrb, int nv, int C, int mode, const double *__restrict__ partial, int m, int j,
+                           double *__restrict__ H, double *__restrict__ coef, double *__restrict__ hn) {
+    const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (o >= (int64_t)nv * C) return;
+    const int k = (int)(o / C), d = (int)(o % C);
+    double s = 0.0;
+    for (int rb = lane; rb < nrb; rb += 32) s += partial[((int64_t)rb * nv + k) * C + d];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane != 0) return;
+    if (mode == RF_NORM) {
+        const double nr = sqrt(s);
+        if (j >= 0) H[((int64_t)d * m + j) * (m + 1) + j + 1] = nr;
+        hn[d] = nr;
+        return;
+    }
+    double *hcol = H + ((int64_t)d * m + j) * (m + 1);
+    hcol[k] = mode == RF_SET ? s : hcol[k] + s;
+    coef[o] = s;
+}
+
+// w[d][i] -= sum_{k < nv} coef[k * C + d] V_k[d][i]
+__global__ void k_rupdate(int64_t n, int C, int nv, const double *__restrict__ V, int64_t vstride,
+                          const double *__restrict__ coef, double *__restrict__ w) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * C) return;
+    const int d = (int)(e / n);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = 0;
+    for (; k + 3 < nv; k += 4) {
+        a0 += coef[(k + 0) * C + d] * V[(int64_t)(k + 0) * vstride + e];
+        a1 += coef[(k + 1) * C + d] * V[(int64_t)(k + 1) * vstride + e];
+        a2 += coef[(k + 2) * C + d] * V[(int64_t)(k + 2) * vstride + e];
+        a3 += coef[(k + 3) * C + d] * V[(int64_t)(k + 3) * vstride + e];
+    }
+    for (; k < nv; ++k) a0 += coef[k * C + d] * V[(int64_t)k * vstride + e];
+    w[e] -= (a0 + a1) + (a2 + a3);
+}
+
+// v[d][i] = w[d][i] / hn[d]  (0 when hn = 0: the direction's Krylov space is exhausted)
+__global__ void k_rscale(int64_t n, int C, const double *__restrict__ hn, const double *__restrict__ w,
+                         double *__restrict__ v) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * C) return;
+    const double h = hn[e / n];
+    v[e] = h > 0.0 ? w[e] / h : 0.0;
+}
+
+// ------------------------------------------------------------------ per-shift least squares
+
+struct ShiftDev {
+    int m;
+    int64_t ncols;
+    int C;
+    const double *H;     // [C][m][m + 1]: column j of direction d at (d * m + j) * (m + 1)
+    const int *cdir;     // [ncols] direction of each column
+    const double2 *z;    // [ncols] shift z(omega_c)
+    double *cs;          // [m][ncols]
+    double2 *sn;         // [m][ncols]
+    double2 *g;          // [m + 1][ncols]
+    double2 *Rt;         // [m (m + 1) / 2][ncols] rotated Hbar - z Ibar, column j at j (j + 1) / 2
+    const double *target;  // [C] residual-estimate target per direction
+    int *done;           // [ncols]
+    int *jdone;          // [ncols] Arnoldi steps the column uses
+};
+
+// g0 = ||R_d|| e1 for every column
+__global__ void k_shift_init(ShiftDev st, const double *__restrict__ rn) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.ncols) return;
+    const double r = rn[st.cdir[c]];
+    st.g[c] = make_double2(r, 0.0);
+    st.done[c] = r == 0.0 ? 1 : 0;
+    st.jdone[c] = 0;
+}
+
+// Column j of Hbar - z Ibar for one column: apply the previous rotations, form the new one
+// (complex sine, real cosine), update g; done when |g_{j+1}| <= target or the process
+// broke down (H(j+1, j) = 0: the Krylov space is invariant, the iterate exact).
+__global__ void k_shift_givens(ShiftDev st, int j) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.ncols || st.done[c]) return;
+    const int64_t nc = st.ncols;
+    const int d = st.cdir[c];
+    const double *h = st.H + ((int64_t)d * st.m + j) * (st.m + 1);
+    const double2 zc = st.z[c];
+    double2 *R = st.Rt + (int64_t)j * (j + 1) / 2 * nc;
+    // t_i = h_i - z delta_ij, rotated by G_0 .. G_{j-1}
+    double2 prev = make_double2(h[0] - (j == 0 ? zc.x : 0.0), j == 0 ? -zc.y : 0.0);
+    for (int i = 0; i < j; ++i) {
+        const double2 nxt = make_double2(h[i + 1] - (i + 1 == j ? zc.x : 0.0), i + 1 == j ? -zc.y : 0.0);
+        const double cs = st.cs[(int64_t)i * nc + c];
+        const double2 sn = st.sn[(int64_t)i * nc + c];
+        R[(int64_t)i * nc + c] = c_add(c_scale(cs, prev), c_mul(sn, nxt));
+        prev = c_sub(c_scale(cs, nxt), c_conjmul(sn, prev));
+    }
+    const double hb = h[j + 1];   // ||w|| >= 0
+    const double na = sqrt(c_abs2(prev));
+    const double nu = sqrt(na * na + hb * hb);
+    double cs;
+    double2 sn, rdiag;
+    if (nu == 0.0) {
+        cs = 1.0;
+        sn = make_double2(0.0, 0.0);
+        rdiag = prev;
+    } else if (na == 0.0) {
+        cs = 0.0;
+        sn = make_double2(1.0, 0.0);
+        rdiag = make_double2(hb, 0.0);
+    } else {
+        const double2 ph = c_scale(1.0 / na, prev);
+        cs = na / nu;
+        sn = c_scale(hb / nu, ph);
+        rdiag = c_scale(nu, ph);
+    }
+    st.cs[(int64_t)j * nc + c] = cs;
+    st.sn[(int64_t)j * nc + c] = sn;
+    R[(int64_t)j * nc + c] = rdiag;
+    const double2 gj = st.g[(int64_t)j * nc + c];
+    const double2 g1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));   // -conj(sn) g_j
+    st.g[(int64_t)(j + 1) * nc + c] = g1;
+    st.g[(int64_t)j * nc + c] = c_scale(cs, gj);
+    if (sqrt(c_abs2(g1)) <= st.target[d] || hb == 0.0 || nu == 0.0) {
+        st.done[c] = 1;
+        st.jdone[c] = j + 1;
+    }
+}
+
+// y = R^{-1} g over the column's jdone steps (columns still open use jlast + 1)
+__global__ void k_shift_backsolve(ShiftDev st, int jlast, double2 *__restrict__ y) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.ncols) return;
+    const int64_t nc = st.ncols;
+    const int jd = st.done[c] ? st.jdone[c] : jlast + 1;
+    st.jdone[c] = jd;
+    for (int l = jd - 1; l >= 0; --l) {
+        double2 s = st.g[(int64_t)l * nc + c];
+        for (int k = l + 1; k < jd; ++k)
+            s = c_sub(s, c_mul(st.Rt[((int64_t)k * (k + 1) / 2 + l) * nc + c], y[(int64_t)k * nc + c]));
+        y[(int64_t)l * nc + c] = c_div(s, st.Rt[((int64_t)l * (l + 1) / 2 + l) * nc + c]);
+    }
+}
+
+// q[i][c] = sum_{k < jdone_c} V_k[d_c][i] y[k][c]
+__global__ void k_shift_combine(int64_t n, int64_t nc, const double *__restrict__ V, int64_t vstride,
+                                const double2 *__restrict__ y, const int *__restrict__ jdone,
+                                const int *__restrict__ cdir, double2 *__restrict__ q) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nc) return;
+    const int64_t i = e / nc, c = e - i * nc;
+    const double *v = V + (int64_t)cdir[c] * n + i;
+    const int jd = jdone[c];
+    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    int k = 0;
+    for (; k + 1 < jd; k += 2) {
+        const double v0 = v[(int64_t)k * vstride], v1 = v[(int64_t)(k + 1) * vstride];
+        const double2 y0 = y[(int64_t)k * nc + c], y1 = y[(int64_t)(k + 1) * nc + c];
+        a.x += v0 * y0.x;
+        a.y += v0 * y0.y;
+        b.x += v1 * y1.x;
+        b.y += v1 * y1.y;
+    }
+    if (k < jd) {
+        const double v0 = v[(int64_t)k * vstride];
+        const double2 y0 = y[(int64_t)k * nc + c];
+        a.x += v0 * y0.x;
+        a.y += v0 * y0.y;
+    }
+    q[e] = c_add(a, b);
+}
+
+__global__ void k_shift_z(int64_t nc, int ndir, const double *__restrict__ omega, double n0, double tau,
+                          double2 *__restrict__ z) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double w = omega[c / ndir];   // Eq. 12
+    const double f = -w / (2.0 * n0 * tau);
+    z[c] = make_double2(f * w * tau, f);
+}
+
+// ------------------------------------------------------------------ host
+
+struct Arnoldi {
+    wfq_geom *g;
+    cudaStream_t s;
+    int64_t n;
+    int C;
+    int64_t rpb;
+    int nrb;
+    DevBuf<float> xh, xl;
+    DevBuf<double> U, partial, coef;
+
+    int init(wfq_geom *geom, int ndir, int m, cudaStream_t stream) {
+        g = geom;
+        s = stream;
+        n = g->n;
+        C = ndir;
+        rpb = std::max<int64_t>(1024, round_up((n + 2 * g->ctx->num_sms - 1) / (2 * g->ctx->num_sms), 256));
+        nrb = (int)((n + rpb - 1) / rpb);
+        WFQ_TRY(xh.alloc(g->ctx, (size_t)n * C, s));
+        WFQ_TRY(xl.alloc(g->ctx, (size_t)n * C, s));
+        WFQ_TRY(U.alloc(g->ctx, (size_t)n * C, s));
+        WFQ_TRY(partial.alloc(g->ctx, (size_t)nrb * (m + 1) * C, s));
+        WFQ_TRY(coef.alloc(g->ctx, (size_t)(m + 1) * C, s));
+        return WFQ_OK;
+    }
+
+    // u = D v for the C direction vectors v (double-float products)
+    int dmul(const double *v, double *u) {
+        k_split_real<<<nblk(n * C), 256, 0, s>>>(n * C, v, xh.ptr, xl.ptr); note_launch();
+        const unsigned blocks = (unsigned)((n + GV_WARPS * GV_ROWS - 1) / (GV_WARPS * GV_ROWS));
+        const double dbytes = 8.0 * (double)n * (double)(g->Dfh ? g->ldf : n);
+        for (int d0 = 0; d0 < C; d0 += 4) {
+            KScope ks(g->ctx, WFQ_KT_DGEMV_DF, s, dbytes);
+            const int cg = std::min(4, C - d0);
+            const float *ph = xh.ptr + (int64_t)d0 * n, *pl = xl.ptr + (int64_t)d0 * n;
+            double *pu = u + (int64_t)d0 * n;
+            const bool pl_ = g->Dfh != nullptr;
+#define WFQ_GV(CC)                                                                                                  \
+    if (pl_)                                                                                                        \
+        k_dgemv_df<CC, true><<<blocks, GV_WARPS * 32, 0, s>>>(n, g->ldf, g->Dfh, g->Dfl, nullptr, ph, pl, pu);      \
+    else                                                                                                            \
+        k_dgemv_df<CC, false><<<blocks, GV_WARPS * 32, 0, s>>>(n, n, nullptr, nullptr, g->D64, ph, pl, pu);
+            switch (cg) {
+                case 1: WFQ_GV(1) break;
+                case 2: WFQ_GV(2) break;
+                case 3: WFQ_GV(3) break;
+                default: WFQ_GV(4) break;
+            }
+#undef WFQ_GV
+            note_launch();
+        }
+        WFQ_CUDA(cudaGetLastError());
+        return WFQ_OK;
+    }
+
+    // w = (Kbar - P) u
+    int sparse(const double *u, double *w) {
+        KScope ks(g->ctx, WFQ_KT_SPARSE, s);
+        k_sparse_real<<<nblk(n), 256, 0, s>>>(n, C, g->rowptr, g->col, g->val64, u, w); note_launch();
+        WFQ_CUDA(cudaGetLastError());
+        return WFQ_OK;
+    }
+
+    // dots of w with nv vectors V_0.. (stride vstride), finished into H column j / coef / hn
+    int dots(const double *V, int64_t vstride, int nv, const double *w, int mode, int m, int j, double *H, double *hn) {
+        dim3 grid((unsigned)nrb, (unsigned)((nv + KV - 1) / KV), (unsigned)C);
+        k_rdot_part<<<grid, 256, 0, s>>>(n, C, nv, V, vstride, w, rpb, partial.ptr); note_launch();
+        k_rdot_fin<<<nblk((int64_t)nv * C * 32), 256, 0, s>>>(nrb, nv, C, mode, partial.ptr, m, j, H, coef.ptr, hn); note_launch();
+        WFQ_CUDA(cudaGetLastError());
+        return WFQ_OK;
+    }
+};
+
+}  // namespace
+
+int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
+    if (!g->Dfh && !g->D64)
+        return fail(WFQ_EUNSUPPORTED, "shifted GMRES needs a stored D (WFQ_STORE_F32X2 or WFQ_STORE_FP64)");
+    wfq_ctx *ctx = g->ctx;
+    const int64_t n = g->n, nf = a.nfreq, C = a.ndir, nc = nf * C;
+    int m = a.m > 0 ? a.m : 600;
+    m = std::max(1, std::min(m, a.max_iter));
+    if ((double)n * C * (2 * m + 1) * 8.0 > 0.5 * 284e9)
+        return fail(WFQ_ENOMEM, "shifted GMRES basis (Arnoldi vectors and their D products) does not fit: lower m");
+
+    Arnoldi ar;
+    WFQ_TRY(ar.init(g, (int)C, m, s));
+    const int64_t vstride = n * C;
+    DevBuf<double> V, DV, H, hn, R, dirs, om, cs, target;
+    DevBuf<double2> z, sn, gv, Rt, y, dq;
+    DevBuf<int> cdir, done, jdone;
+    WFQ_TRY(V.alloc(ctx, (size_t)(m + 1) * vstride, s));
+    WFQ_TRY(DV.alloc(ctx, (size_t)m * vstride, s));   // D v_k of every Arnoldi vector used
+    WFQ_TRY(H.alloc(ctx, (size_t)C * m * (m + 1), s));
+    WFQ_TRY(hn.alloc(ctx, C, s));
+    WFQ_TRY(R.alloc(ctx, (size_t)n * C, s));
+    WFQ_TRY(dirs.alloc(ctx, 3 * C, s));
+    WFQ_TRY(om.alloc(ctx, nf, s));
+    WFQ_TRY(cs.alloc(ctx, (size_t)m * nc, s));
+    WFQ_TRY(target.alloc(ctx, C, s));
+    WFQ_TRY(z.alloc(ctx, nc, s));
+    WFQ_TRY(sn.alloc(ctx, (size_t)m * nc, s));
+    WFQ_TRY(gv.alloc(ctx, (size_t)(m + 1) * nc, s));
+    WFQ_TRY(Rt.alloc(ctx, (size_t)m * (m + 1) / 2 * nc, s));
+    WFQ_TRY(y.alloc(ctx, (size_t)m * nc, s));
+    WFQ_TRY(cdir.alloc(ctx, nc, s));
+    WFQ_TRY(done.alloc(ctx, nc, s));
+    WFQ_TRY(jdone.alloc(ctx, nc, s));
+    std::vector<int> cdir_h(nc);
+    for (int64_t c = 0; c < nc; ++c) cdir_h[c] = (int)(c % C);
+    WFQ_CUDA(cudaMemcpyAsync(cdir.ptr, cdir_h.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    WFQ_CUDA(cudaMemcpyAsync(dirs.ptr, a.dirs, sizeof(double) * 3 * C, cudaMemcpyHostToDevice, s));
+    WFQ_CUDA(cudaMemcpyAsync(om.ptr, a.omega, sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+    WFQ_CUDA(cudaMemsetAsync(H.ptr, 0, sizeof(double) * C * m * (m + 1), s));
+    k_shift_z<<<nblk(nc), 256, 0, s>>>(nc, (int)C, om.ptr, g->p.n0, g->p.tau, z.ptr); note_launch();
+
+    // v_0 = R_d / ||R_d||
+    WFQ_TRY(launch_rhs(g, (int)C, dirs.ptr, a.E0, R.ptr, s));
+    k_take_rhs<<<nblk(n * C), 256, 0, s>>>(n, (int)C, R.ptr, ar.U.ptr); note_launch();
+    WFQ_TRY(ar.dots(ar.U.ptr, 0, 1, ar.U.ptr, RF_NORM, m, -1, H.ptr, hn.ptr));
+    k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, ar.U.ptr, V.ptr); note_launch();
+    std::vector<double> rn_h(C), tg(C);
+    WFQ_CUDA(cudaMemcpyAsync(rn_h.data(), hn.ptr, sizeof(double) * C, cudaMemcpyDeviceToHost, s));
+    WFQ_CUDA(cudaStreamSynchronize(s));
+    for (int64_t d = 0; d < C; ++d) tg[d] = 0.5 * a.rel_tol * rn_h[d];
+    WFQ_CUDA(cudaMemcpyAsync(target.ptr, tg.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s));
+    ShiftDev st{m, nc, (int)C, H.ptr, cdir.ptr, z.ptr, cs.ptr, sn.ptr, gv.ptr, Rt.ptr, target.ptr, done.ptr, jdone.ptr};
+    k_shift_init<<<nblk(nc), 256, 0, s>>>(st, hn.ptr); note_launch();
+    WFQ_CUDA(cudaGetLastError());
+
+    std::vector<int> done_h(nc);
+    int jlast = -1;
+    for (int j = 0; j < m; ++j) {
+        const double *vj = V.ptr + (int64_t)j * vstride;
+        double *dvj = DV.ptr + (int64_t)j * vstride;
+        double *w = V.ptr + (int64_t)(j + 1) * vstride;
+        WFQ_TRY(ar.dmul(vj, dvj));
+        WFQ_TRY(ar.sparse(dvj, w));
+        {
+            KScope ko(ctx, WFQ_KT_ORTHO, s);
+            for (int pass = 0; pass < 2; ++pass) {
+                WFQ_TRY(ar.dots(V.ptr, vstride, j + 1, w, pass == 0 ? RF_SET : RF_ADD, m, j, H.ptr, hn.ptr));
+                k_rupdate<<<nblk(n * C), 256, 0, s>>>(n, (int)C, j + 1, V.ptr, vstride, ar.coef.ptr, w); note_launch();
+            }
+            WFQ_TRY(ar.dots(w, 0, 1, w, RF_NORM, m, j, H.ptr, hn.ptr));
+            k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, w, w); note_launch();
+            k_shift_givens<<<nblk(nc), 256, 0, s>>>(st, j); note_launch();
+            WFQ_CUDA(cudaGetLastError());
+        }
+        jlast = j;
+        if ((j & 3) == 3 || j == m - 1) {
+            WFQ_CUDA(cudaMemcpyAsync(done_h.data(), done.ptr, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+            WFQ_TRY(check_device_error(ctx, s));
+            if (std::all_of(done_h.begin(), done_h.end(), [](int v) { return v != 0; })) break;
+        }
+    }
+    WFQ_TRY(dq.alloc(ctx, (size_t)n * nc, s));
+    k_shift_backsolve<<<nblk(nc), 256, 0, s>>>(st, jlast, y.ptr); note_launch();
+    k_shift_combine<<<nblk(n * nc), 256, 0, s>>>(n, nc, V.ptr, vstride, y.ptr, jdone.ptr, cdir.ptr, a.q); note_launch();
+    k_shift_combine<<<nblk(n * nc), 256, 0, s>>>(n, nc, DV.ptr, vstride, y.ptr, jdone.ptr, cdir.ptr, dq.ptr); note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    std::vector<int> jd_h(nc);
+    WFQ_CUDA(cudaMemcpyAsync(jd_h.data(), jdone.ptr, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+    WFQ_CUDA(cudaStreamSynchronize(s));
+
+    // FP64 true residual of every column; the ones above tol continue in block GMRES(50)
+    return finish_columns(g, a, jd_h, 50, dq.ptr, s);
+}
+
+}  // namespace wfq

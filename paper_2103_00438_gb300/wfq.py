@@ -16,15 +16,15 @@ from . import build as _build
 WFQ_OK = 0
 STATUS = {0: "WFQ_OK", -1: "WFQ_EINVAL", -2: "WFQ_ESINGULAR", -3: "WFQ_ENOMEM", -4: "WFQ_ENOCONV",
           -5: "WFQ_EBREAKDOWN", -6: "WFQ_ETIMEOUT", -7: "WFQ_ECUDA", -8: "WFQ_EUNSUPPORTED"}
-STORE_FP64, STORE_BF16X2 = 1, 2
+STORE_FP64, STORE_BF16X2, STORE_F32X2 = 1, 2, 4
 PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2
 
 # every symbol include/wfq.h declares
 EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry", "wfq_free_geometry",
-           "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_qmr",
+           "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_gmres_shifted", "wfq_solve_qmr",
            "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc",
            "wfq_server_create", "wfq_server_submit", "wfq_server_poll", "wfq_server_destroy"]
-KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE, KT_ORTHO, KT_RESIDUAL = 0, 1, 2, 3, 4
+KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE, KT_ORTHO, KT_RESIDUAL, KT_DGEMV_DF = 0, 1, 2, 3, 4, 5
 
 
 class WfqError(RuntimeError):
@@ -71,6 +71,7 @@ def load(path: str | None = None):
     L.wfq_rhs.argtypes = [_P, INT, _P, D, _P, _P]
     L.wfq_solve_gmres.argtypes = [_P, I64, _P, INT, _P, D, INT, D, INT, INT, _P, _P, _P]
     L.wfq_solve_qmr.argtypes = [_P, I64, _P, INT, _P, D, D, INT, INT, INT, _P, _P, _P]
+    L.wfq_solve_gmres_shifted.argtypes = [_P, I64, _P, INT, _P, D, INT, D, INT, INT, _P, _P, _P]
     L.wfq_polarizability.argtypes = [_P, I64, _P, D, _P, _P]
     L.wfq_apply_mixed_noalloc.argtypes = [_P, I64, _P, _P, _P, _P]
     L.wfq_server_create.argtypes = [_P, INT, I64, INT, ctypes.POINTER(_P)]
@@ -238,7 +239,7 @@ class Geometry:
         _check(_lib.wfq_rhs(self.h, len(d), _ptr(d), float(E0), po, _stream_handle(stream)))
         return out
 
-    def _solve(self, qmr, omega, dirs, E0, m, rel_tol, max_iter, prec, refine_every, out, stream):
+    def _solve(self, kind, omega, dirs, E0, m, rel_tol, max_iter, prec, refine_every, out, stream):
         om = _host_f64(np.atleast_1d(omega))
         d = _host_f64(np.atleast_2d(dirs))
         ncols = len(om) * len(d)
@@ -246,7 +247,11 @@ class Geometry:
             out = np.empty((self.n, ncols), dtype=np.complex128)
         out, pq = _buf(out, np.complex128, self.n, self.n * ncols, True, "out")
         stats = (Stats * ncols)()
-        if qmr:
+        if kind == "shifted":
+            rc = _lib.wfq_solve_gmres_shifted(self.h, len(om), _ptr(om), len(d), _ptr(d), float(E0), int(m),
+                                              float(rel_tol), int(max_iter), int(prec), pq,
+                                              ctypes.cast(stats, _P), _stream_handle(stream))
+        elif kind == "qmr":
             rc = _lib.wfq_solve_qmr(self.h, len(om), _ptr(om), len(d), _ptr(d), float(E0), float(rel_tol),
                                     int(max_iter), int(prec), int(refine_every), pq,
                                     ctypes.cast(stats, _P), _stream_handle(stream))
@@ -263,11 +268,16 @@ class Geometry:
     def solve_gmres(self, omega, dirs, E0=1.0, m=0, rel_tol=1e-8, max_iter=1000, prec=PREC_FP64,
                     out=None, stream=None):
         """q (n, nfreq*ndir) complex128, per-column stats, overall status name."""
-        return self._solve(False, omega, dirs, E0, m, rel_tol, max_iter, prec, 0, out, stream)
+        return self._solve("gmres", omega, dirs, E0, m, rel_tol, max_iter, prec, 0, out, stream)
+
+    def solve_gmres_shifted(self, omega, dirs, E0=1.0, m_max=0, rel_tol=1e-8, max_iter=4000, prec=PREC_MIXED,
+                            out=None, stream=None):
+        """Shifted GMRES: one real Arnoldi per direction for all frequencies (wfq_solve_gmres_shifted)."""
+        return self._solve("shifted", omega, dirs, E0, m_max, rel_tol, max_iter, prec, 0, out, stream)
 
     def solve_qmr(self, omega, dirs, E0=1.0, rel_tol=1e-8, max_iter=1000, prec=PREC_FP64, refine_every=0,
                   out=None, stream=None):
-        return self._solve(True, omega, dirs, E0, 0, rel_tol, max_iter, prec, refine_every, out, stream)
+        return self._solve("qmr", omega, dirs, E0, 0, rel_tol, max_iter, prec, refine_every, out, stream)
 
     def polarizability(self, q, E0=1.0, stream=None):
         """alpha (ncols, 3) complex128 from q (n, ncols) complex128 (host or device)."""

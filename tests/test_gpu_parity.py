@@ -338,6 +338,82 @@ def test_batched_columns_each_match_oracle(W, ctx, orc, S):
                 assert st[c]["rel_residual"] <= tol
 
 
+# ----------------------------------------------------------------------------- shifted GMRES
+
+def test_shifted_gmres_iterates_match_oracle_gmres(W, ctx, orc, S):
+    """After k Arnoldi steps every (omega, direction) column of the shifted solver holds
+    the k-step unrestarted GMRES iterate of its own system (A - z(omega) I) q = R_dir:
+    the Krylov space of A - zI from R does not depend on z."""
+    xyz = S.honeycomb_flake(6)
+    p = _carbon(S)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.3, 0.7, 1.4])
+    dirs = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    op = sysm.operator()
+    for k in (1, 3, 8):
+        q, st, status = g.solve_gmres_shifted(om, dirs, m_max=k, rel_tol=1e-14, max_iter=k, prec=W.PREC_FP64)
+        assert status == "WFQ_ENOCONV"
+        for f in range(len(om)):
+            for d in range(2):
+                c = f * 2 + d
+                assert st[c]["iters"] == k
+                R = sysm.rhs(dirs[d]).astype(complex)
+                qo, _ = op.gmres(sysm.z(om[f]), R, restart=0, rel_tol=1e-300, max_iter=k)
+                assert np.linalg.norm(q[:, c] - qo) <= 1e-10 * np.linalg.norm(qo), (k, f, d)
+
+
+@pytest.mark.parametrize("store", ["f32x2", "fp64"])
+def test_shifted_gmres_columns_match_lu(W, ctx, orc, S, store):
+    """All frequencies x directions from the shared real Arnoldi processes; each column's
+    alpha equals its own oracle LU solve and its FP64 residual meets the tolerance without
+    any block-GMRES continuation."""
+    xyz = S.nanotube(5, 5, 30)          # 600 atoms, axis z
+    p = S.carbon_params(1.04)
+    flag = W.STORE_F32X2 if store == "f32x2" else W.STORE_FP64
+    g = W.Geometry(ctx, xyz, p, store=flag)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.15, 0.6, 1.1, 1.9])
+    dirs = np.eye(3)
+    q, st, status = g.solve_gmres_shifted(om, dirs, rel_tol=1e-10, max_iter=2000, prec=W.PREC_FP64)
+    assert status == "WFQ_OK"
+    al = g.polarizability(q)
+    for f in range(4):
+        for d in range(3):
+            c = f * 3 + d
+            q_lu, _ = sysm.solve(om[f], dirs[d], method="lu")
+            a_ref = orc.alpha(xyz, q_lu)
+            assert np.abs(al[c] - a_ref).max() <= 1e-8 * np.abs(a_ref).max(), (f, d)
+            assert st[c]["rel_residual"] <= 1e-10 and st[c]["restarts"] == 0, st[c]
+            assert abs(q[:, c].sum()) <= 1e-10 * np.abs(q[:, c]).sum()
+
+
+def test_shifted_gmres_capped_basis_continues_in_block_gmres(W, ctx, orc, S):
+    """A basis cap far below the iterations needed: every column continues from its
+    shifted iterate in mixed block GMRES(50) with FP64 refinement and meets the bar."""
+    wl = S.workload("flake1k")
+    xyz, p = wl["xyz"], wl["params"]
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2 | W.STORE_BF16X2)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.2, 0.52, 1.3])
+    q, st, status = g.solve_gmres_shifted(om, [[1.0, 0, 0]], m_max=6, rel_tol=1e-8, max_iter=3000,
+                                          prec=W.PREC_MIXED)
+    assert status == "WFQ_OK"
+    al = g.polarizability(q)
+    for f in range(3):
+        q_lu, _ = sysm.solve(om[f], np.array([1.0, 0, 0]), method="lu")
+        a_ref = orc.alpha(xyz, q_lu)
+        assert np.abs(al[f] - a_ref).max() <= 1e-6 * np.abs(a_ref).max(), f
+        assert st[f]["rel_residual"] <= 1e-8 and st[f]["restarts"] >= 1 and st[f]["iters"] > 6
+
+
+def test_shifted_gmres_needs_stored_d(W, ctx, S):
+    g = W.Geometry(ctx, S.honeycomb_flake(3), _carbon(S), store=W.STORE_BF16X2)
+    with pytest.raises(W.WfqError) as e:
+        g.solve_gmres_shifted(S.ev([0.5]), [[1.0, 0, 0]])
+    assert e.value.code == -8
+
+
 # ----------------------------------------------------------------------------- edge cases
 
 def test_edge_single_atom_and_dimer(W, ctx, orc, S):
