@@ -278,8 +278,12 @@ int wfq_polarizability(wfq_geom *g, int64_t ncols, const double *q, double E0,
  * A worker that becomes free takes the oldest request whose batch fits the memory budget
  * and merges into the same block solve every queued request on the same geometry with
  * the same settings (continuous batching), up to max_columns complex columns; batches on
- * different workers run concurrently.  Solves are mixed-precision GMRES(m) with FP64
- * refinement (as wfq_solve_gmres with WFQ_PREC_MIXED).
+ * different workers run concurrently.  A batch on a geometry with a stored D
+ * (WFQ_STORE_F32X2 or WFQ_STORE_FP64) is solved by shifted GMRES (as
+ * wfq_solve_gmres_shifted: one real Arnoldi process per distinct field direction of the
+ * batch for all its frequencies; m is not used, continuations run GMRES(50)); otherwise
+ * by mixed-precision GMRES(m) with FP64 refinement (as wfq_solve_gmres with
+ * WFQ_PREC_MIXED).
  *   budget_bytes: device memory the batches in flight may use together (Krylov bases,
  *   blocks, scratch; the geometries themselves are not counted).  A batch that alone
  *   exceeds it still runs when nothing else is in flight. */

@@ -236,7 +236,10 @@ struct SolveArgs {
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
 int solve_qmr(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
 // Shifted GMRES (one real Arnoldi per direction for all frequencies); a.m caps the basis.
+// Explicit column lists (a.col_omega / a.col_dir over a.ndir directions) are accepted.
 int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
+// Device bytes a shifted solve of ncols columns over ndir directions allocates (m: basis cap).
+size_t shifted_footprint(const wfq_geom *g, int64_t ncols, int ndir, int m);
 // FP64 true residual of every column of a (iterate in a.q); columns above a.rel_tol continue
 // in block GMRES(m) at a.prec.  iters: Krylov steps already spent per column.  dq: D a.q
 // (n x ncols) when the caller has it, else null (computed with double-float products).

@@ -11,6 +11,9 @@
 //     Kbar), up to a column limit.  Requests that arrive while others run are picked up
 //     as soon as a worker and memory free up; batches on different streams overlap on
 //     the device.
+//   - Solver of a batch: shifted GMRES when the structure has a stored D (one real
+//     Arnoldi process per distinct field direction serves every frequency of every merged
+//     request), else mixed block GMRES(m) with FP64 refinement.
 //   - Each request's result (its columns of q, its per-column statistics) is written to
 //     the caller's host buffers; submit / completion times give its latency.
 #include <chrono>
@@ -46,6 +49,32 @@ struct Request {
     bool done = false;
     int batch_columns = 0;
 };
+
+// Structures with a stored D (FP32 pair planes or FP64) are served by shifted GMRES; the
+// others by mixed block GMRES(m).
+bool use_shifted(const wfq_geom *g) { return g->Dfh != nullptr || g->D64 != nullptr; }
+
+// Distinct field directions of a batch (exact comparison) and, per request, the index of
+// each of its directions in that list.
+int unique_dirs(const std::vector<Request *> &batch, std::vector<double> &dirs, std::vector<std::vector<int>> &map) {
+    dirs.clear();
+    map.assign(batch.size(), {});
+    for (size_t k = 0; k < batch.size(); ++k) {
+        const Request *r = batch[k];
+        for (int d = 0; d < r->ndir; ++d) {
+            const double *v = &r->dirs[3 * (size_t)d];
+            int found = -1;
+            for (size_t u = 0; u < dirs.size() / 3 && found < 0; ++u)
+                if (dirs[3 * u] == v[0] && dirs[3 * u + 1] == v[1] && dirs[3 * u + 2] == v[2]) found = (int)u;
+            if (found < 0) {
+                found = (int)(dirs.size() / 3);
+                dirs.insert(dirs.end(), v, v + 3);
+            }
+            map[k].push_back(found);
+        }
+    }
+    return (int)(dirs.size() / 3);
+}
 
 bool same_settings(const Request *a, const Request *b) {
     return a->g == b->g && a->E0 == b->E0 && a->m == b->m && a->rel_tol == b->rel_tol &&
@@ -94,7 +123,16 @@ struct wfq_server {
                         cols += r->ncols();
                     }
                 }
-                const size_t need = wfq::solve_footprint(head->g, cols, head->m, WFQ_PREC_MIXED);
+                size_t need;
+                if (use_shifted(head->g)) {
+                    std::vector<Request *> pb;
+                    for (size_t i : pick) pb.push_back(queue[i]);
+                    std::vector<double> ud;
+                    std::vector<std::vector<int>> um;
+                    need = wfq::shifted_footprint(head->g, cols, unique_dirs(pb, ud, um), 0);
+                } else {
+                    need = wfq::solve_footprint(head->g, cols, head->m, WFQ_PREC_MIXED);
+                }
                 if (in_use == 0 || in_use + need <= budget) {
                     batch.clear();
                     for (size_t k = pick.size(); k-- > 0;) {
@@ -143,20 +181,21 @@ struct wfq_server {
         using namespace wfq;
         Request *head = batch.front();
         wfq_geom *g = head->g;
-        // merged column list: each request keeps its own (omega x dirs) columns in order
+        // merged column list: each request keeps its own (omega x dirs) columns in order;
+        // directions shared by several requests are one direction of the batch
         std::vector<double> col_om, dirs;
         std::vector<int> col_dir;
         std::vector<int64_t> first_col;
-        int dir_base = 0;
-        for (Request *r : batch) {
+        std::vector<std::vector<int>> dmap;
+        const int ndir_u = unique_dirs(batch, dirs, dmap);
+        for (size_t k = 0; k < batch.size(); ++k) {
+            Request *r = batch[k];
             first_col.push_back((int64_t)col_om.size());
             for (double om : r->omega)
                 for (int d = 0; d < r->ndir; ++d) {
                     col_om.push_back(om);
-                    col_dir.push_back(dir_base + d);
+                    col_dir.push_back(dmap[k][d]);
                 }
-            dirs.insert(dirs.end(), r->dirs.begin(), r->dirs.end());
-            dir_base += r->ndir;
             r->batch_columns = 0;
         }
         const int64_t cc = (int64_t)col_om.size(), n = g->n;
@@ -166,7 +205,7 @@ struct wfq_server {
         std::vector<wfq_stats> st(cc);
         if ((rc = q.alloc(g->ctx, (size_t)n * cc, s)) == WFQ_OK) {
             SolveArgs a;
-            a.ndir = dir_base;
+            a.ndir = ndir_u;
             a.dirs = dirs.data();
             a.col_omega = col_om.data();
             a.col_dir = col_dir.data();
@@ -178,7 +217,12 @@ struct wfq_server {
             a.prec = WFQ_PREC_MIXED;
             a.q = q.ptr;
             a.stats = st.data();
-            rc = solve_gmres(g, a, s);
+            if (use_shifted(g)) {
+                a.m = 0;   // basis cap: the solver's default; continuations run GMRES(50)
+                rc = solve_gmres_shifted(g, a, s);
+            } else {
+                rc = solve_gmres(g, a, s);
+            }
         }
         for (size_t k = 0; k < batch.size(); ++k) {
             Request *r = batch[k];
@@ -256,7 +300,8 @@ int wfq_server_submit(wfq_server *sv, wfq_geom *g, int64_t nfreq, const double *
     if (g->ctx != sv->ctx) return fail(WFQ_EINVAL, "geometry belongs to another context");
     const int64_t cols = nfreq * ndir;
     if (cols > sv->max_cols) return fail(WFQ_EINVAL, "request has more columns than the server's batch limit");
-    if (solve_footprint(g, cols, m, WFQ_PREC_MIXED) > sv->budget)
+    const size_t need = use_shifted(g) ? shifted_footprint(g, cols, ndir, 0) : solve_footprint(g, cols, m, WFQ_PREC_MIXED);
+    if (need > sv->budget)
         return fail(WFQ_ENOMEM, "request footprint exceeds the server's memory budget");
     auto *r = new Request;
     r->g = g;

@@ -399,11 +399,11 @@ __global__ void k_shift_combine(int64_t n, int64_t nc, const double *__restrict_
     q[e] = c_add(a, b);
 }
 
-__global__ void k_shift_z(int64_t nc, int ndir, const double *__restrict__ omega, double n0, double tau,
+__global__ void k_shift_z(int64_t nc, const double *__restrict__ col_omega, double n0, double tau,
                           double2 *__restrict__ z) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
-    const double w = omega[c / ndir];   // Eq. 12
+    const double w = col_omega[c];   // Eq. 12
     const double f = -w / (2.0 * n0 * tau);
     z[c] = make_double2(f * w * tau, f);
 }
@@ -484,11 +484,20 @@ struct Arnoldi {
 
 }  // namespace
 
+size_t shifted_footprint(const wfq_geom *g, int64_t ncols, int ndir, int m) {
+    if (m <= 0) m = 600;
+    const size_t n = (size_t)g->n, C = (size_t)ndir, nc = (size_t)ncols;
+    size_t b = (size_t)(2 * m + 1) * n * C * 8;                                // Arnoldi vectors, D v_k
+    b += (size_t)m * (m + 1) / 2 * nc * 16 + (size_t)(3 * m + 2) * nc * 16;   // rotated H, rotations, g, y
+    b += n * nc * 16 * 9;                                                     // q, D q, residual blocks
+    return b;
+}
+
 int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     if (!g->Dfh && !g->D64)
         return fail(WFQ_EUNSUPPORTED, "shifted GMRES needs a stored D (WFQ_STORE_F32X2 or WFQ_STORE_FP64)");
     wfq_ctx *ctx = g->ctx;
-    const int64_t n = g->n, nf = a.nfreq, C = a.ndir, nc = nf * C;
+    const int64_t n = g->n, C = a.ndir, nc = a.col_omega ? a.ncols : a.nfreq * C;
     int m = a.m > 0 ? a.m : 600;
     m = std::max(1, std::min(m, a.max_iter));
     if ((double)n * C * (2 * m + 1) * 8.0 > 0.5 * 284e9)
@@ -506,7 +515,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     WFQ_TRY(hn.alloc(ctx, C, s));
     WFQ_TRY(R.alloc(ctx, (size_t)n * C, s));
     WFQ_TRY(dirs.alloc(ctx, 3 * C, s));
-    WFQ_TRY(om.alloc(ctx, nf, s));
+    WFQ_TRY(om.alloc(ctx, nc, s));
     WFQ_TRY(cs.alloc(ctx, (size_t)m * nc, s));
     WFQ_TRY(target.alloc(ctx, C, s));
     WFQ_TRY(z.alloc(ctx, nc, s));
@@ -517,13 +526,18 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     WFQ_TRY(cdir.alloc(ctx, nc, s));
     WFQ_TRY(done.alloc(ctx, nc, s));
     WFQ_TRY(jdone.alloc(ctx, nc, s));
+    // column c: frequency om_h[c], direction cdir_h[c] (explicit lists, or c = f * ndir + d)
     std::vector<int> cdir_h(nc);
-    for (int64_t c = 0; c < nc; ++c) cdir_h[c] = (int)(c % C);
+    std::vector<double> om_h(nc);
+    for (int64_t c = 0; c < nc; ++c) {
+        cdir_h[c] = a.col_dir ? a.col_dir[c] : (int)(c % C);
+        om_h[c] = a.col_omega ? a.col_omega[c] : a.omega[c / C];
+    }
     WFQ_CUDA(cudaMemcpyAsync(cdir.ptr, cdir_h.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     WFQ_CUDA(cudaMemcpyAsync(dirs.ptr, a.dirs, sizeof(double) * 3 * C, cudaMemcpyHostToDevice, s));
-    WFQ_CUDA(cudaMemcpyAsync(om.ptr, a.omega, sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+    WFQ_CUDA(cudaMemcpyAsync(om.ptr, om_h.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, s));
     WFQ_CUDA(cudaMemsetAsync(H.ptr, 0, sizeof(double) * C * m * (m + 1), s));
-    k_shift_z<<<nblk(nc), 256, 0, s>>>(nc, (int)C, om.ptr, g->p.n0, g->p.tau, z.ptr); note_launch();
+    k_shift_z<<<nblk(nc), 256, 0, s>>>(nc, om.ptr, g->p.n0, g->p.tau, z.ptr); note_launch();
 
     // v_0 = R_d / ||R_d||
     WFQ_TRY(launch_rhs(g, (int)C, dirs.ptr, a.E0, R.ptr, s));
@@ -532,7 +546,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, ar.U.ptr, V.ptr); note_launch();
     std::vector<double> rn_h(C), tg(C);
     WFQ_CUDA(cudaMemcpyAsync(rn_h.data(), hn.ptr, sizeof(double) * C, cudaMemcpyDeviceToHost, s));
-    WFQ_CUDA(cudaStreamSynchronize(s));
+    WFQ_CUDA(cudaStreamSynchronize(s));   // also completes the cdir_h / om_h uploads
     for (int64_t d = 0; d < C; ++d) tg[d] = 0.5 * a.rel_tol * rn_h[d];
     WFQ_CUDA(cudaMemcpyAsync(target.ptr, tg.data(), sizeof(double) * C, cudaMemcpyHostToDevice, s));
     ShiftDev st{m, nc, (int)C, H.ptr, cdir.ptr, z.ptr, cs.ptr, sn.ptr, gv.ptr, Rt.ptr, target.ptr, done.ptr, jdone.ptr};

@@ -11,10 +11,12 @@ pytestmark = pytest.mark.gpu
 def test_server_results_same_alone_and_in_the_mix(S):
     from paper_2103_00438_gb300 import wfq
     ctx = wfq.Context(0)
-    store = wfq.STORE_FP64 | wfq.STORE_BF16X2
+    # stored D: batches run shifted GMRES; the bf16-only geometry: mixed block GMRES
+    store = wfq.STORE_F32X2 | wfq.STORE_BF16X2
     geoms = [wfq.Geometry(ctx, S.honeycomb_flake(10), S.carbon_params(1.51), store=store),
-             wfq.Geometry(ctx, S.nanotube(5, 5, 40), S.carbon_params(1.04), store=store),
-             wfq.Geometry(ctx, S.random_cluster(900, seed=4), dict(S.carbon_params(1.2), r0=2.7), store=store)]
+             wfq.Geometry(ctx, S.nanotube(5, 5, 40), S.carbon_params(1.04), store=wfq.STORE_FP64),
+             wfq.Geometry(ctx, S.random_cluster(900, seed=4), dict(S.carbon_params(1.2), r0=2.7),
+                          store=wfq.STORE_BF16X2)]
     rng = np.random.default_rng(7)
     reqs = []
     for k in range(14):
