@@ -67,9 +67,10 @@ def parse():
 
 # D storage per workload: FP64 + bf16 planes where both fit; bf16 planes only for the 150k
 # sphere (FP64 D would be 180 GB); nothing stored for the 1M-atom disk (matrix-free).
-def store_for(name, wfq):
+def store_for(name, wfq, solver="gmres"):
     if name == "sphere150k":
-        return wfq.STORE_BF16X2
+        # the FP32 pair planes alone are 180 GB; the bf16 planes alone 90 GB
+        return wfq.STORE_F32X2 if solver == "shifted" else wfq.STORE_BF16X2
     if name in ("disk1m", "disk100k"):
         return 0
     return wfq.STORE_FP64 | wfq.STORE_BF16X2 | wfq.STORE_F32X2
@@ -98,6 +99,11 @@ def workload(name):
     if name == "cnt8k":   # small case for ncu captures: same tube, 205 cells, same block width
         wl = S.workload("cnt20k")
         wl["xyz"] = S.nanotube(10, 10, 205)
+        return wl
+    if name == "sphere30k":   # the 150k sphere's family and band at 30k atoms (solver comparisons)
+        wl = S.workload("sphere150k")
+        a = 4.23
+        wl["xyz"] = S.fcc_sphere(a, S.fcc_sphere_radius_for(30_000, a), 0.05, seed=20210301)
         return wl
     if name == "disk100k":   # small matrix-free case for ncu captures: same disk family, 18.3 nm
         wl = S.workload("disk1m")
@@ -263,7 +269,7 @@ def run_ours(args, rank, world, dist):
     n, nf, nd = len(xyz), len(om), len(dirs)
     ncols = nf * nd
     ctx = wfq.Context(local)
-    store = store_for(args.workload, wfq)
+    store = store_for(args.workload, wfq, args.solver)
     g = wfq.Geometry(ctx, xyz, p, store=store)
     mode = args.mode or ("apply" if args.workload in ("disk1m", "disk100k") else "solve")
     if mode == "apply":
@@ -368,7 +374,9 @@ def run_ours(args, rank, world, dist):
                                     if args.solver == "shifted" else
                                     "mixed: 3xBF16 D products, complex64 basis, FP64 refinement"),
                       "rel_tol": 1e-8, "parallelism": f"replicas{world}",
-                      "l2": "inputs larger than L2 (bf16 D planes %.2f GB)" % (4.0 * n * n / 1e9)},
+                      "l2": "inputs larger than L2 (%s %.2f GB)" % (
+                          ("FP32 pair D planes", 8.0 * n * n / 1e9) if args.solver == "shifted"
+                          else ("bf16 D planes", 4.0 * n * n / 1e9))},
            "accuracy": {"max_rel_residual": max_res, "columns_converged": good_cols,
                         "iters_min_mean_max": [min(iters), float(np.mean(iters)), max(iters)],
                         "status": status_last},

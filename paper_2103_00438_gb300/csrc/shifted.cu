@@ -57,9 +57,14 @@ __global__ void k_split_real(int64_t total, const double *__restrict__ x, float 
     df_split(x[e], xh[e], xl[e]);
 }
 
-constexpr int GV_ROWS = 2;       // rows per warp
+// Tiling chosen by a sweep at N = 20000 (rows per warp 1-4, 1-8 steps of loads in flight,
+// 4-16 warps, register caps): the kernel is bound by instruction issue of the double-float
+// arithmetic (~12 FP32 instructions per entry and vector), and one row per warp with four
+// 128-column load steps at 64 registers (4 blocks, 32 warps per SM) was fastest.
+constexpr int GV_ROWS = 1;       // rows per warp
 constexpr int GV_TB = 4;         // 128-column steps whose D loads are issued together
 constexpr int GV_WARPS = 8;      // warps per block
+constexpr int GV_MINB = 4;       // resident blocks per SM the register budget must allow
 constexpr int GV_CHUNK = 1024;   // x entries staged in shared memory per step
 
 // U[d][i] = sum_j D_ij x[d][j] for C real vectors (direction-major, length n), with
@@ -70,7 +75,7 @@ constexpr int GV_CHUNK = 1024;   // x entries staged in shared memory per step
 // are conflict-free.  PL: D from the FP32 pair planes (row pitch ld, a multiple of 4, zero
 // beyond n); else split from the FP64 D.  Entries past n contribute zero (x is zero there).
 template <int C, bool PL>
-__global__ void __launch_bounds__(GV_WARPS * 32) k_dgemv_df(int64_t n, int64_t ld, const float *__restrict__ Fh,
+__global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, int64_t ld, const float *__restrict__ Fh,
                                                             const float *__restrict__ Fl,
                                                             const double *__restrict__ D64,
                                                             const float *__restrict__ xh,
@@ -312,16 +317,19 @@ __global__ void k_shift_givens(ShiftDev st, int j) {
     if (c >= st.ncols || st.done[c]) return;
     const int64_t nc = st.ncols;
     const int d = st.cdir[c];
-    const double *h = st.H + ((int64_t)d * st.m + j) * (st.m + 1);
+    const double *__restrict__ h = st.H + ((int64_t)d * st.m + j) * (st.m + 1);
+    const double *__restrict__ csv = st.cs + c;
+    const double2 *__restrict__ snv = st.sn + c;
     const double2 zc = st.z[c];
-    double2 *R = st.Rt + (int64_t)j * (j + 1) / 2 * nc;
-    // t_i = h_i - z delta_ij, rotated by G_0 .. G_{j-1}
+    double2 *__restrict__ R = st.Rt + (int64_t)j * (j + 1) / 2 * nc + c;
+    // t_i = h_i - z delta_ij, rotated by G_0 .. G_{j-1} (loads do not depend on the chain)
     double2 prev = make_double2(h[0] - (j == 0 ? zc.x : 0.0), j == 0 ? -zc.y : 0.0);
+#pragma unroll 4
     for (int i = 0; i < j; ++i) {
         const double2 nxt = make_double2(h[i + 1] - (i + 1 == j ? zc.x : 0.0), i + 1 == j ? -zc.y : 0.0);
-        const double cs = st.cs[(int64_t)i * nc + c];
-        const double2 sn = st.sn[(int64_t)i * nc + c];
-        R[(int64_t)i * nc + c] = c_add(c_scale(cs, prev), c_mul(sn, nxt));
+        const double cs = __ldg(csv + (int64_t)i * nc);
+        const double2 sn = __ldg(snv + (int64_t)i * nc);
+        R[(int64_t)i * nc] = c_add(c_scale(cs, prev), c_mul(sn, nxt));
         prev = c_sub(c_scale(cs, nxt), c_conjmul(sn, prev));
     }
     const double hb = h[j + 1];   // ||w|| >= 0
@@ -345,7 +353,7 @@ __global__ void k_shift_givens(ShiftDev st, int j) {
     }
     st.cs[(int64_t)j * nc + c] = cs;
     st.sn[(int64_t)j * nc + c] = sn;
-    R[(int64_t)j * nc + c] = rdiag;
+    R[(int64_t)j * nc] = rdiag;
     const double2 gj = st.g[(int64_t)j * nc + c];
     const double2 g1 = make_double2(-(sn.x * gj.x + sn.y * gj.y), -(sn.x * gj.y - sn.y * gj.x));   // -conj(sn) g_j
     st.g[(int64_t)(j + 1) * nc + c] = g1;
@@ -363,11 +371,21 @@ __global__ void k_shift_backsolve(ShiftDev st, int jlast, double2 *__restrict__ 
     const int64_t nc = st.ncols;
     const int jd = st.done[c] ? st.jdone[c] : jlast + 1;
     st.jdone[c] = jd;
+    const double2 *__restrict__ Rt = st.Rt + c;
+    double2 *__restrict__ yc = y + c;
     for (int l = jd - 1; l >= 0; --l) {
-        double2 s = st.g[(int64_t)l * nc + c];
-        for (int k = l + 1; k < jd; ++k)
-            s = c_sub(s, c_mul(st.Rt[((int64_t)k * (k + 1) / 2 + l) * nc + c], y[(int64_t)k * nc + c]));
-        y[(int64_t)l * nc + c] = c_div(s, st.Rt[((int64_t)l * (l + 1) / 2 + l) * nc + c]);
+        // four independent partial sums of R(l, k) y_k, k > l
+        double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
+        int k = l + 1;
+        for (; k + 3 < jd; k += 4) {
+            a0 = c_add(a0, c_mul(Rt[((int64_t)k * (k + 1) / 2 + l) * nc], yc[(int64_t)k * nc]));
+            a1 = c_add(a1, c_mul(Rt[((int64_t)(k + 1) * (k + 2) / 2 + l) * nc], yc[(int64_t)(k + 1) * nc]));
+            a2 = c_add(a2, c_mul(Rt[((int64_t)(k + 2) * (k + 3) / 2 + l) * nc], yc[(int64_t)(k + 2) * nc]));
+            a3 = c_add(a3, c_mul(Rt[((int64_t)(k + 3) * (k + 4) / 2 + l) * nc], yc[(int64_t)(k + 3) * nc]));
+        }
+        for (; k < jd; ++k) a0 = c_add(a0, c_mul(Rt[((int64_t)k * (k + 1) / 2 + l) * nc], yc[(int64_t)k * nc]));
+        const double2 s = c_sub(st.g[(int64_t)l * nc + c], c_add(c_add(a0, a1), c_add(a2, a3)));
+        yc[(int64_t)l * nc] = c_div(s, Rt[((int64_t)l * (l + 1) / 2 + l) * nc]);
     }
 }
 
