@@ -42,8 +42,18 @@ __device__ __forceinline__ float d_pair_f32(float4 a, float4 b, float wa2) {
     return erff(r2 * rinv * rsqrtf(s2)) * rinv;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+// 1/sqrt(x) in one MUFU operation (flush-to-zero approximate form, relative error below
+// 2^-22; r^2 is never subnormal here and the result is kept to 16 bits in the hi/lo split).
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// (a, b) -> bf16 pair (a in the low half), one conversion instruction for both
+__device__ __forceinline__ uint32_t bf16x2_rn(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
@@ -222,28 +232,26 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
                 const float4 *atoms_s = reinterpret_cast<const float4 *>(smem + (size_t)s * p.stage_bytes + atoms_off);
                 {
                     const int kb0 = k0 + kc * 8;
-                    float dv[8], r2v[8], s2v[8], rinv[8];
-                    uint32_t near = 0;
+                    float dv[8], r2v[8], s2v[8];
+                    bool near = false;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         // far pairs: 1/r from one rsqrt (erf(r/sigma) rounds to 1 in FP32)
                         const float4 b = atoms_s[kc * 8 + e];
                         const float dx = ai.x - b.x, dy = ai.y - b.y, dz = ai.z - b.z;
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float s2 = wa2 + b.w * b.w;
-                        const float ri = rsqrtf(r2);
+                        const float s2 = fmaf(b.w, b.w, wa2);
                         r2v[e] = r2;
                         s2v[e] = s2;
-                        rinv[e] = ri;
-                        dv[e] = ri;
-                        near |= (r2 < 16.0f * s2 ? 1u : 0u) << e;
+                        dv[e] = rsqrt_mufu(r2);
+                        near = near || (r2 < 16.0f * s2);
                     }
                     // near pairs (rare: only tiles close to the diagonal) take the erf branch,
                     // entered by a warp only when one of its lanes needs it
-                    if (__any_sync(0xffffffffu, near != 0u)) {
+                    if (__any_sync(0xffffffffu, near)) {
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
-                            if (near & (1u << e)) dv[e] = erff(r2v[e] * rinv[e] * rsqrtf(s2v[e])) * rinv[e];
+                            if (r2v[e] < 16.0f * s2v[e]) dv[e] = erff(r2v[e] * dv[e] * rsqrtf(s2v[e])) * dv[e];
                     }
                     if (gi >= kb0 && gi < kb0 + 8) {                      // D_ii = eta_i
 #pragma unroll
@@ -255,14 +263,14 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
                         for (int e = 0; e < 8; ++e)
                             if (!row_ok || kb0 + e >= p.n) dv[e] = 0.f;
                     }
+                    // hi = bf16(D), lo = bf16(D - hi), two entries per conversion
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(dv[e]), h1 = __float2bfloat16_rn(dv[e + 1]);
-                        const __nv_bfloat16 l0 = __float2bfloat16_rn(dv[e] - __bfloat162float(h0));
-                        const __nv_bfloat16 l1 = __float2bfloat16_rn(dv[e + 1] - __bfloat162float(h1));
-                        hw[e >> 1] = pack_bf16(h0, h1);
-                        lw[e >> 1] = pack_bf16(l0, l1);
+                        const uint32_t h = bf16x2_rn(dv[e], dv[e + 1]);
+                        const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
+                        hw[e >> 1] = h;
+                        lw[e >> 1] = bf16x2_rn(dv[e] - h0, dv[e + 1] - h1);
                     }
                     // 64-byte swizzle: 16-byte chunk index XOR (row / 2) mod 4
                     const uint32_t off = (uint32_t)row * 64u + (uint32_t)((kc ^ ((row >> 1) & 3)) * 16);

@@ -164,19 +164,38 @@ __global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, 
     }
 }
 
-// W[d][i] = sum_p Kbar_ip (U[d][j_p] - U[d][i]) = ((Kbar - P) U)_i  (Eq. 16-17), FP64.
-__global__ void k_sparse_real(int64_t n, int C, const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                              const double *__restrict__ val, const double *__restrict__ U, double *__restrict__ W) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// W[d][i] = sum_p Kbar_ip (U[d][j_p] - U[d][i]) = ((Kbar - P) U)_i  (Eq. 16-17), FP64, for
+// directions d0 .. d0 + CG - 1.  One warp per row: the lanes stride over the row's
+// neighbours (coalesced CSR reads, each entry read once for all CG directions), then sum
+// in a fixed butterfly order.
+template <int CG>
+__global__ void __launch_bounds__(256) k_sparse_real(int64_t n, int d0, const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                     const double *__restrict__ U, double *__restrict__ W) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;   // whole warp
     const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
-    for (int d = 0; d < C; ++d) {
-        const double *u = U + (int64_t)d * n;
-        const double ui = u[i];
-        double acc = 0.0;
-        for (int64_t p = p0; p < p1; ++p) acc += val[p] * (u[col[p]] - ui);
-        W[(int64_t)d * n + i] = acc;
+    double ui[CG], acc[CG];
+#pragma unroll
+    for (int d = 0; d < CG; ++d) {
+        ui[d] = U[(int64_t)(d0 + d) * n + i];
+        acc[d] = 0.0;
     }
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+        const double v = val[p];
+        const int64_t j = col[p];
+#pragma unroll
+        for (int d = 0; d < CG; ++d) acc[d] += v * (U[(int64_t)(d0 + d) * n + j] - ui[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < CG; ++d) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], off);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int d = 0; d < CG; ++d) W[(int64_t)(d0 + d) * n + i] = acc[d];
 }
 
 // W[d][i] = R[i * C + d]   (atom-major right-hand sides -> direction-major vectors)
@@ -485,7 +504,16 @@ struct Arnoldi {
     // w = (Kbar - P) u
     int sparse(const double *u, double *w) {
         KScope ks(g->ctx, WFQ_KT_SPARSE, s);
-        k_sparse_real<<<nblk(n), 256, 0, s>>>(n, C, g->rowptr, g->col, g->val64, u, w); note_launch();
+        const unsigned blocks = nblk(n * 32);
+        for (int d0 = 0; d0 < C; d0 += 4) {
+            switch (std::min(4, C - d0)) {
+                case 1: k_sparse_real<1><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
+                case 2: k_sparse_real<2><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
+                case 3: k_sparse_real<3><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
+                default: k_sparse_real<4><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
+            }
+            note_launch();
+        }
         WFQ_CUDA(cudaGetLastError());
         return WFQ_OK;
     }
