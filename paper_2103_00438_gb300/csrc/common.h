@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -86,6 +87,10 @@ struct wfq_ctx {
     cudaMemPool_t pool = nullptr;
     int *dev_err = nullptr;   // device flag: non-zero after a bounded wait in a kernel gave up
     wfq::KernelTimer timer;
+    // autotuner results: kernel tiling chosen by timing, per problem key (kept across
+    // geometries of the same shape)
+    std::mutex tune_mu;
+    std::map<int64_t, int> tuned;
 };
 
 struct wfq_geom {

@@ -57,25 +57,26 @@ __global__ void k_split_real(int64_t total, const double *__restrict__ x, float 
     df_split(x[e], xh[e], xl[e]);
 }
 
-// Tiling chosen by a sweep at N = 20000 (rows per warp 1-4, 1-8 steps of loads in flight,
-// 4-16 warps, register caps): the kernel is bound by instruction issue of the double-float
-// arithmetic (~12 FP32 instructions per entry and vector), and one row per warp with four
-// 128-column load steps at 64 registers (4 blocks, 32 warps per SM) was fastest.
-constexpr int GV_ROWS = 1;       // rows per warp
-constexpr int GV_TB = 4;         // 128-column steps whose D loads are issued together
+// Tilings of the double-float GEMV: rows per warp, 128-column load steps in flight per lane,
+// resident blocks per SM the register budget must allow.  The kernel is bound by
+// instruction issue of the double-float arithmetic (~12 FP32 instructions per entry and
+// vector) as much as by memory; which tiling overlaps the two best depends on N and on the
+// number of vectors, so the first product of each shape times all of them on the real
+// operands and keeps the fastest (autotune below).  A sweep at N = 20000 found 0.75-0.85 ms
+// per launch for these four and 0.9-1.4 ms for wider or 16-warp tilings.
 constexpr int GV_WARPS = 8;      // warps per block
-constexpr int GV_MINB = 4;       // resident blocks per SM the register budget must allow
 constexpr int GV_CHUNK = 1024;   // x entries staged in shared memory per step
+constexpr int GV_NTILINGS = 4;
 
 // U[d][i] = sum_j D_ij x[d][j] for C real vectors (direction-major, length n), with
-// double-float products.  Each warp owns GV_ROWS rows and reads them with 16-byte loads
-// (four consecutive j per lane), GV_TB steps of 128 columns at a time so that 2 * GV_ROWS *
-// GV_TB independent loads per lane are in flight before any is used; x is staged per
+// double-float products.  Each warp owns ROWS rows and reads them with 16-byte loads
+// (four consecutive j per lane), TB steps of 128 columns at a time so that 2 * ROWS * TB
+// independent loads per lane are in flight before any is used; x is staged per
 // chunk in shared memory as separate hi / lo planes so that a quarter-warp's 16-byte reads
 // are conflict-free.  PL: D from the FP32 pair planes (row pitch ld, a multiple of 4, zero
 // beyond n); else split from the FP64 D.  Entries past n contribute zero (x is zero there).
-template <int C, bool PL>
-__global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, int64_t ld, const float *__restrict__ Fh,
+template <int C, bool PL, int ROWS, int TB, int MINB>
+__global__ void __launch_bounds__(GV_WARPS * 32, MINB) k_dgemv_df(int64_t n, int64_t ld, const float *__restrict__ Fh,
                                                             const float *__restrict__ Fl,
                                                             const double *__restrict__ D64,
                                                             const float *__restrict__ xh,
@@ -83,10 +84,10 @@ __global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, 
     __shared__ __align__(16) float sxh[C][GV_CHUNK];
     __shared__ __align__(16) float sxl[C][GV_CHUNK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row0 = ((int64_t)blockIdx.x * GV_WARPS + warp) * GV_ROWS;
-    float sh[GV_ROWS][C], sl[GV_ROWS][C];
+    const int64_t row0 = ((int64_t)blockIdx.x * GV_WARPS + warp) * ROWS;
+    float sh[ROWS][C], sl[ROWS][C];
 #pragma unroll
-    for (int r = 0; r < GV_ROWS; ++r)
+    for (int r = 0; r < ROWS; ++r)
 #pragma unroll
         for (int d = 0; d < C; ++d) sh[r][d] = sl[r][d] = 0.f;
 
@@ -101,13 +102,13 @@ __global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, 
         __syncthreads();
         const int64_t trem = (n - j0 + 127) / 128;
         const int tend = trem < GV_CHUNK / 128 ? (int)trem : GV_CHUNK / 128;
-        for (int t0 = 0; t0 < tend; t0 += GV_TB) {
-            float4 dh[GV_TB][GV_ROWS], dl[GV_TB][GV_ROWS];
+        for (int t0 = 0; t0 < tend; t0 += TB) {
+            float4 dh[TB][ROWS], dl[TB][ROWS];
 #pragma unroll
-            for (int t = 0; t < GV_TB; ++t) {
+            for (int t = 0; t < TB; ++t) {
                 const int64_t j = j0 + (t0 + t) * 128 + lane * 4;
 #pragma unroll
-                for (int r = 0; r < GV_ROWS; ++r) {
+                for (int r = 0; r < ROWS; ++r) {
                     const int64_t i = row0 + r;
                     if (i >= n || j >= n) {
                         dh[t][r] = dl[t][r] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -125,14 +126,14 @@ __global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, 
                 }
             }
 #pragma unroll
-            for (int t = 0; t < GV_TB; ++t) {
+            for (int t = 0; t < TB; ++t) {
                 const int jl = (t0 + t) * 128 + lane * 4;
 #pragma unroll
                 for (int d = 0; d < C; ++d) {
                     const float4 xh4 = *reinterpret_cast<const float4 *>(&sxh[d][jl]);
                     const float4 xl4 = *reinterpret_cast<const float4 *>(&sxl[d][jl]);
 #pragma unroll
-                    for (int r = 0; r < GV_ROWS; ++r) {
+                    for (int r = 0; r < ROWS; ++r) {
                         df_mac(dh[t][r].x, dl[t][r].x, xh4.x, xl4.x, sh[r][d], sl[r][d]);
                         df_mac(dh[t][r].y, dl[t][r].y, xh4.y, xl4.y, sh[r][d], sl[r][d]);
                         df_mac(dh[t][r].z, dl[t][r].z, xh4.z, xl4.z, sh[r][d], sl[r][d]);
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, 
     }
     // warp sums in double-float, fixed butterfly order
 #pragma unroll
-    for (int r = 0; r < GV_ROWS; ++r)
+    for (int r = 0; r < ROWS; ++r)
 #pragma unroll
         for (int d = 0; d < C; ++d)
 #pragma unroll
@@ -155,12 +156,35 @@ __global__ void __launch_bounds__(GV_WARPS * 32, GV_MINB) k_dgemv_df(int64_t n, 
             }
     if (lane == 0) {
 #pragma unroll
-        for (int r = 0; r < GV_ROWS; ++r) {
+        for (int r = 0; r < ROWS; ++r) {
             const int64_t i = row0 + r;
             if (i < n)
 #pragma unroll
                 for (int d = 0; d < C; ++d) U[(int64_t)d * n + i] = (double)sh[r][d] + (double)sl[r][d];
         }
+    }
+}
+
+template <int C, bool PL>
+void launch_dgemv(int tiling, int64_t n, int64_t ld, const float *Fh, const float *Fl, const double *D64,
+                  const float *xh, const float *xl, double *U, cudaStream_t s) {
+    const unsigned b1 = (unsigned)((n + GV_WARPS - 1) / GV_WARPS), b2 = (unsigned)((n + 2 * GV_WARPS - 1) / (2 * GV_WARPS));
+    switch (tiling) {
+        case 1: k_dgemv_df<C, PL, 2, 4, 3><<<b2, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+        case 2: k_dgemv_df<C, PL, 2, 2, 4><<<b2, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+        case 3: k_dgemv_df<C, PL, 1, 8, 3><<<b1, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+        default: k_dgemv_df<C, PL, 1, 4, 4><<<b1, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+    }
+}
+
+template <bool PL>
+void launch_dgemv_c(int cg, int tiling, int64_t n, int64_t ld, const float *Fh, const float *Fl, const double *D64,
+                    const float *xh, const float *xl, double *U, cudaStream_t s) {
+    switch (cg) {
+        case 1: launch_dgemv<1, PL>(tiling, n, ld, Fh, Fl, D64, xh, xl, U, s); break;
+        case 2: launch_dgemv<2, PL>(tiling, n, ld, Fh, Fl, D64, xh, xl, U, s); break;
+        case 3: launch_dgemv<3, PL>(tiling, n, ld, Fh, Fl, D64, xh, xl, U, s); break;
+        default: launch_dgemv<4, PL>(tiling, n, ld, Fh, Fl, D64, xh, xl, U, s); break;
     }
 }
 
@@ -273,22 +297,34 @@ __global__ void k_rdot_fin(int nrb, int nv, int C, int mode, const double *__res
     coef[o] = s;
 }
 
-// w[d][i] -= sum_{k < nv} coef[k * C + d] V_k[d][i]
-__global__ void k_rupdate(int64_t n, int C, int nv, const double *__restrict__ V, int64_t vstride,
-                          const double *__restrict__ coef, double *__restrict__ w) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * C) return;
-    const int d = (int)(e / n);
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int k = 0;
-    for (; k + 3 < nv; k += 4) {
-        a0 += coef[(k + 0) * C + d] * V[(int64_t)(k + 0) * vstride + e];
-        a1 += coef[(k + 1) * C + d] * V[(int64_t)(k + 1) * vstride + e];
-        a2 += coef[(k + 2) * C + d] * V[(int64_t)(k + 2) * vstride + e];
-        a3 += coef[(k + 3) * C + d] * V[(int64_t)(k + 3) * vstride + e];
+// w[d][i] -= sum_{k < nv} coef[k * C + d] V_k[d][i].  A block takes 32 consecutive
+// elements; its 8 warps take the vectors k = warp, warp + 8, ... (coalesced 256-byte rows of
+// each V_k), and the 8 partial sums are added in a fixed order.
+constexpr int RU_SLICES = 8;
+__global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate(int64_t n, int C, int nv, const double *__restrict__ V,
+                                                            int64_t vstride, const double *__restrict__ coef,
+                                                            double *__restrict__ w) {
+    __shared__ double part[RU_SLICES][32];
+    const int el = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 32 + el;
+    double a0 = 0.0, a1 = 0.0;
+    if (e < n * C) {
+        const int d = (int)(e / n);
+        int k = sl;
+        for (; k + RU_SLICES < nv; k += 2 * RU_SLICES) {
+            a0 += coef[k * C + d] * V[(int64_t)k * vstride + e];
+            a1 += coef[(k + RU_SLICES) * C + d] * V[(int64_t)(k + RU_SLICES) * vstride + e];
+        }
+        if (k < nv) a0 += coef[k * C + d] * V[(int64_t)k * vstride + e];
     }
-    for (; k < nv; ++k) a0 += coef[k * C + d] * V[(int64_t)k * vstride + e];
-    w[e] -= (a0 + a1) + (a2 + a3);
+    part[sl][el] = a0 + a1;
+    __syncthreads();
+    if (sl == 0 && e < n * C) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < RU_SLICES; ++q) t += part[q][el];
+        w[e] -= t;
+    }
 }
 
 // v[d][i] = w[d][i] / hn[d]  (0 when hn = 0: the direction's Krylov space is exhausted)
@@ -472,29 +508,62 @@ struct Arnoldi {
         return WFQ_OK;
     }
 
+    // Tiling of the GEMV for `cg` vectors on this geometry's shape: looked up in the
+    // context's autotuner cache, else chosen now by timing every tiling twice on the real
+    // operands (xh / xl already split) and kept for later products of the same shape.
+    int tiling_for(int cg, bool pl, const float *ph, const float *pl_x, double *pu) {
+        const int64_t key = ((int64_t)n << 8) | ((int64_t)cg << 1) | (pl ? 1 : 0);
+        {
+            std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
+            auto it = g->ctx->tuned.find(key);
+            if (it != g->ctx->tuned.end()) return it->second;
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            cudaGetLastError();
+            if (e0) cudaEventDestroy(e0);
+            return 0;
+        }
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int t = 0; t < GV_NTILINGS; ++t) {
+            float ms = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {   // the first of the three warms up
+                if (rep == 1) cudaEventRecord(e0, s);
+                if (pl) launch_dgemv_c<true>(cg, t, n, g->ldf, g->Dfh, g->Dfl, nullptr, ph, pl_x, pu, s);
+                else launch_dgemv_c<false>(cg, t, n, n, nullptr, nullptr, g->D64, ph, pl_x, pu, s);
+                note_launch();
+            }
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lk(g->ctx->tune_mu);
+        g->ctx->tuned[key] = best;
+        return best;
+    }
+
     // u = D v for the C direction vectors v (double-float products)
     int dmul(const double *v, double *u) {
         k_split_real<<<nblk(n * C), 256, 0, s>>>(n * C, v, xh.ptr, xl.ptr); note_launch();
-        const unsigned blocks = (unsigned)((n + GV_WARPS * GV_ROWS - 1) / (GV_WARPS * GV_ROWS));
         const double dbytes = 8.0 * (double)n * (double)(g->Dfh ? g->ldf : n);
+        const bool pl = g->Dfh != nullptr;
         for (int d0 = 0; d0 < C; d0 += 4) {
-            KScope ks(g->ctx, WFQ_KT_DGEMV_DF, s, dbytes);
             const int cg = std::min(4, C - d0);
-            const float *ph = xh.ptr + (int64_t)d0 * n, *pl = xl.ptr + (int64_t)d0 * n;
+            const float *ph = xh.ptr + (int64_t)d0 * n, *pxl = xl.ptr + (int64_t)d0 * n;
             double *pu = u + (int64_t)d0 * n;
-            const bool pl_ = g->Dfh != nullptr;
-#define WFQ_GV(CC)                                                                                                  \
-    if (pl_)                                                                                                        \
-        k_dgemv_df<CC, true><<<blocks, GV_WARPS * 32, 0, s>>>(n, g->ldf, g->Dfh, g->Dfl, nullptr, ph, pl, pu);      \
-    else                                                                                                            \
-        k_dgemv_df<CC, false><<<blocks, GV_WARPS * 32, 0, s>>>(n, n, nullptr, nullptr, g->D64, ph, pl, pu);
-            switch (cg) {
-                case 1: WFQ_GV(1) break;
-                case 2: WFQ_GV(2) break;
-                case 3: WFQ_GV(3) break;
-                default: WFQ_GV(4) break;
-            }
-#undef WFQ_GV
+            const int tiling = tiling_for(cg, pl, ph, pxl, pu);
+            KScope ks(g->ctx, WFQ_KT_DGEMV_DF, s, dbytes);
+            if (pl) launch_dgemv_c<true>(cg, tiling, n, g->ldf, g->Dfh, g->Dfl, nullptr, ph, pxl, pu, s);
+            else launch_dgemv_c<false>(cg, tiling, n, n, nullptr, nullptr, g->D64, ph, pxl, pu, s);
             note_launch();
         }
         WFQ_CUDA(cudaGetLastError());
@@ -611,7 +680,8 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
             KScope ko(ctx, WFQ_KT_ORTHO, s);
             for (int pass = 0; pass < 2; ++pass) {
                 WFQ_TRY(ar.dots(V.ptr, vstride, j + 1, w, pass == 0 ? RF_SET : RF_ADD, m, j, H.ptr, hn.ptr));
-                k_rupdate<<<nblk(n * C), 256, 0, s>>>(n, (int)C, j + 1, V.ptr, vstride, ar.coef.ptr, w); note_launch();
+                k_rupdate<<<nblk(n * C, 32), 32 * RU_SLICES, 0, s>>>(n, (int)C, j + 1, V.ptr, vstride, ar.coef.ptr, w);
+                note_launch();
             }
             WFQ_TRY(ar.dots(w, 0, 1, w, RF_NORM, m, j, H.ptr, hn.ptr));
             k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, w, w); note_launch();

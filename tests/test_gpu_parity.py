@@ -115,17 +115,19 @@ def test_apply_mixed_within_derived_bound(W, ctx, orc, S, n, ncplx):
     assert worst <= TAU_MIXED
 
 
-@pytest.mark.parametrize("n,ncplx", [(1000, 3), (1333, 7), (2049, 40)])
-def test_apply_double_float_within_derived_bound(W, ctx, orc, S, n, ncplx):
+@pytest.mark.parametrize("n,ncplx,store", [(1000, 3, "fp64"), (1333, 7, "fp64"), (2049, 40, "fp64"),
+                                           (1333, 7, "f32x2"), (2049, 40, "f32x2")])
+def test_apply_double_float_within_derived_bound(W, ctx, orc, S, n, ncplx, store):
     """Double-float D products: operands split into float pairs (48 significant bits),
     products and sums error-free up to ~2^-48 each, so per element
         |dy_i| <= TAU_DF * (sum_p Kbar_ip (s_i + s_j) + |z| |x_i|),  s = |D| |x|,
     with TAU_DF = 8 * 2^-48 * sqrt(N): rounding errors of 2^-48 per step that add up
-    like a random walk over the N-term sum, with a factor 8 of margin."""
+    like a random walk over the N-term sum, with a factor 8 of margin.  D split from the
+    stored FP64 D, or read from the stored FP32 pair planes (the same 48-bit pair)."""
     TAU_DF = 8 * 2.0 ** -48 * np.sqrt(n)
     xyz = S.random_cluster(n, seed=n + 5)
     p = _carbon(S, r0=2.7)
-    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 if store == "fp64" else W.STORE_F32X2)
     sysm = orc.System(xyz, p)
     om = S.ev(np.linspace(0.2, 1.9, ncplx))
     x = S.random_complex((n, ncplx), seed=11)
@@ -405,6 +407,25 @@ def test_shifted_gmres_capped_basis_continues_in_block_gmres(W, ctx, orc, S):
         a_ref = orc.alpha(xyz, q_lu)
         assert np.abs(al[f] - a_ref).max() <= 1e-6 * np.abs(a_ref).max(), f
         assert st[f]["rel_residual"] <= 1e-8 and st[f]["restarts"] >= 1 and st[f]["iters"] > 6
+
+
+def test_shifted_gmres_bitwise_repeatable_across_contexts(W, S):
+    """The shifted solver's D product is autotuned per context (the first product of a shape
+    times every tiling); every tiling sums each row in the same order, so two contexts give
+    bitwise-identical solutions whichever tilings they picked."""
+    xyz = S.nanotube(5, 5, 60)
+    p = S.carbon_params(1.04)
+    om = S.ev([0.3, 1.2])
+    out = []
+    for _ in range(2):
+        c = W.Context(0)
+        g = W.Geometry(c, xyz, p, store=W.STORE_F32X2)
+        q, st, status = g.solve_gmres_shifted(om, np.eye(3), rel_tol=1e-9, prec=W.PREC_FP64)
+        assert status == "WFQ_OK"
+        out.append(q.copy())
+        g.close()
+        c.close()
+    assert np.array_equal(out[0], out[1])
 
 
 def test_shifted_gmres_needs_stored_d(W, ctx, S):
