@@ -876,7 +876,9 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
             if (std::all_of(done_h.begin(), done_h.end(), [](int v) { return v != 0; })) break;
         }
         if (jlast >= 0) {
-            k_backsolve<<<nblocks(na), 256, 0, s>>>(na, jlast, st, y.ptr); note_launch();
+            // one thread per column, a serial FP64 chain each: spread over many SMs (few FP64
+            // units per SM on GB300)
+            k_backsolve<<<nblocks(na, 4), 4, 0, s>>>(na, jlast, st, y.ptr); note_launch();
             k_combine<VT><<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)na, jlast + 1, V.ptr, vstride, y.ptr, jdone.ptr,
                                                        cm.Ya.ptr); note_launch();
             k_scatter_add<<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)na, cc, cm.idx.ptr, cm.Ya.ptr, a.q); note_launch();

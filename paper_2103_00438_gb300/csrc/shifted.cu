@@ -32,6 +32,11 @@ namespace {
 
 inline unsigned nblk(int64_t total, int t = 256) { return (unsigned)((total + t - 1) / t); }
 
+// Threads per block of the one-thread-per-column FP64 kernels (Givens step, back
+// substitution): their work is a serial FP64 chain per column, and GB300 has only about two
+// FP64 FMAs per clock per SM, so the columns are spread over many SMs instead of filling one.
+constexpr int PER_COLUMN_BLOCK = 4;
+
 __device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 c_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 c_scale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
@@ -367,27 +372,26 @@ __global__ void k_shift_init(ShiftDev st, const double *__restrict__ rn) {
 // Column j of Hbar - z Ibar for one column: apply the previous rotations, form the new one
 // (complex sine, real cosine), update g; done when |g_{j+1}| <= target or the process
 // broke down (H(j+1, j) = 0: the Krylov space is invariant, the iterate exact).
-__global__ void k_shift_givens(ShiftDev st, int j) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st.ncols || st.done[c]) return;
+// h: entries 0..j of column j of the column's direction; hb = H(j+1, j).
+__device__ void shift_givens_col(const ShiftDev &st, int64_t c, int j, const double *h, double hb) {
+    if (st.done[c]) return;
     const int64_t nc = st.ncols;
     const int d = st.cdir[c];
-    const double *__restrict__ h = st.H + ((int64_t)d * st.m + j) * (st.m + 1);
     const double *__restrict__ csv = st.cs + c;
     const double2 *__restrict__ snv = st.sn + c;
     const double2 zc = st.z[c];
     double2 *__restrict__ R = st.Rt + (int64_t)j * (j + 1) / 2 * nc + c;
+    auto hv = [&](int i) { return h[i]; };
     // t_i = h_i - z delta_ij, rotated by G_0 .. G_{j-1} (loads do not depend on the chain)
-    double2 prev = make_double2(h[0] - (j == 0 ? zc.x : 0.0), j == 0 ? -zc.y : 0.0);
+    double2 prev = make_double2(hv(0) - (j == 0 ? zc.x : 0.0), j == 0 ? -zc.y : 0.0);
 #pragma unroll 4
     for (int i = 0; i < j; ++i) {
-        const double2 nxt = make_double2(h[i + 1] - (i + 1 == j ? zc.x : 0.0), i + 1 == j ? -zc.y : 0.0);
+        const double2 nxt = make_double2(hv(i + 1) - (i + 1 == j ? zc.x : 0.0), i + 1 == j ? -zc.y : 0.0);
         const double cs = __ldg(csv + (int64_t)i * nc);
         const double2 sn = __ldg(snv + (int64_t)i * nc);
         R[(int64_t)i * nc] = c_add(c_scale(cs, prev), c_mul(sn, nxt));
         prev = c_sub(c_scale(cs, nxt), c_conjmul(sn, prev));
     }
-    const double hb = h[j + 1];   // ||w|| >= 0
     const double na = sqrt(c_abs2(prev));
     const double nu = sqrt(na * na + hb * hb);
     double cs;
@@ -417,6 +421,13 @@ __global__ void k_shift_givens(ShiftDev st, int j) {
         st.done[c] = 1;
         st.jdone[c] = j + 1;
     }
+}
+
+__global__ void k_shift_givens(ShiftDev st, int j) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.ncols) return;
+    const double *h = st.H + ((int64_t)st.cdir[c] * st.m + j) * (st.m + 1);
+    shift_givens_col(st, c, j, h, h[j + 1]);
 }
 
 // y = R^{-1} g over the column's jdone steps (columns still open use jlast + 1)
@@ -553,7 +564,8 @@ struct Arnoldi {
 
     // u = D v for the C direction vectors v (double-float products)
     int dmul(const double *v, double *u) {
-        k_split_real<<<nblk(n * C), 256, 0, s>>>(n * C, v, xh.ptr, xl.ptr); note_launch();
+        k_split_real<<<nblk(n * C), 256, 0, s>>>(n * C, v, xh.ptr, xl.ptr);
+        note_launch();
         const double dbytes = 8.0 * (double)n * (double)(g->Dfh ? g->ldf : n);
         const bool pl = g->Dfh != nullptr;
         for (int d0 = 0; d0 < C; d0 += 4) {
@@ -685,7 +697,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
             }
             WFQ_TRY(ar.dots(w, 0, 1, w, RF_NORM, m, j, H.ptr, hn.ptr));
             k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, w, w); note_launch();
-            k_shift_givens<<<nblk(nc), 256, 0, s>>>(st, j); note_launch();
+            k_shift_givens<<<nblk(nc, PER_COLUMN_BLOCK), PER_COLUMN_BLOCK, 0, s>>>(st, j); note_launch();
             WFQ_CUDA(cudaGetLastError());
         }
         jlast = j;
@@ -696,7 +708,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         }
     }
     WFQ_TRY(dq.alloc(ctx, (size_t)n * nc, s));
-    k_shift_backsolve<<<nblk(nc), 256, 0, s>>>(st, jlast, y.ptr); note_launch();
+    k_shift_backsolve<<<nblk(nc, PER_COLUMN_BLOCK), PER_COLUMN_BLOCK, 0, s>>>(st, jlast, y.ptr); note_launch();
     k_shift_combine<<<nblk(n * nc), 256, 0, s>>>(n, nc, V.ptr, vstride, y.ptr, jdone.ptr, cdir.ptr, a.q); note_launch();
     k_shift_combine<<<nblk(n * nc), 256, 0, s>>>(n, nc, DV.ptr, vstride, y.ptr, jdone.ptr, cdir.ptr, dq.ptr); note_launch();
     WFQ_CUDA(cudaGetLastError());

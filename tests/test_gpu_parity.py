@@ -390,6 +390,26 @@ def test_shifted_gmres_columns_match_lu(W, ctx, orc, S, store):
             assert abs(q[:, c].sum()) <= 1e-10 * np.abs(q[:, c]).sum()
 
 
+def test_shifted_gmres_more_than_four_directions(W, ctx, orc, S):
+    """Five field directions: the D product of the Arnoldi vectors runs in groups of at most
+    four vectors (and the sparse term likewise); every column still equals its LU solve."""
+    xyz = S.nanotube(5, 5, 15)
+    p = S.carbon_params(1.04)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.4, 1.5])
+    dirs = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0], [0.6, 0.8, 0], [0, 0.6, 0.8]])
+    q, st, status = g.solve_gmres_shifted(om, dirs, rel_tol=1e-10, max_iter=2000, prec=W.PREC_FP64)
+    assert status == "WFQ_OK"
+    al = g.polarizability(q)
+    for f in range(2):
+        for d in range(5):
+            c = f * 5 + d
+            q_lu, _ = sysm.solve(om[f], dirs[d], method="lu")
+            a_ref = orc.alpha(xyz, q_lu)
+            assert np.abs(al[c] - a_ref).max() <= 1e-8 * np.abs(a_ref).max(), (f, d)
+
+
 def test_shifted_gmres_capped_basis_continues_in_block_gmres(W, ctx, orc, S):
     """A basis cap far below the iterations needed: every column continues from its
     shifted iterate in mixed block GMRES(50) with FP64 refinement and meets the bar."""
