@@ -77,8 +77,8 @@ def store_for(name, wfq, solver="gmres"):
 
 
 # DRAM bytes per stored D entry that ncu measured for one k_dgemv_df launch (cnt8k, N = 8200:
-# 545.0 MB read + written for 8200 x 8200 entries of the FP32 pair planes).
-DGEMV_DRAM_BYTES_PER_ENTRY = 545.0e6 / (8200.0 * 8200.0)
+# 543.5 MB read + written for 8200 x 8200 entries of the FP32 pair planes).
+DGEMV_DRAM_BYTES_PER_ENTRY = 543.5e6 / (8200.0 * 8200.0)
 
 # Minimum FP32-pipe instructions to generate one D entry as a bf16 hi/lo pair on the
 # matrix-free path: 3 coordinate differences, 3 for r^2, 1 for sigma^2, 1 far/near test,

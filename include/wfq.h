@@ -258,8 +258,11 @@ int wfq_solve_gmres_shifted(wfq_geom *g, int64_t nfreq, const double *omega, int
  * (Section 3; J = D since D A = A^T D, Eq. 18).  The bilinear form u^T D v needs D v,
  * which the operator apply already produces, so each iteration costs one D product.
  * With WFQ_PREC_MIXED the QMR recurrence restarts from the FP64 true residual every
- * `refine_every` iterations (0 = only when its own residual estimate converges).
- * Returns WFQ_EBREAKDOWN if rho or sigma vanishes in some column. */
+ * `refine_every` iterations (0 = when its own residual estimate converges, at the latest
+ * after 300 iterations); a column whose true residual shrank by less than 2x in two
+ * consecutive restarts, or whose recurrence broke down, is finished by plain FP64
+ * GMRES(50) from its iterate.  Returns WFQ_EBREAKDOWN if rho or sigma vanishes in some
+ * column of an FP64 solve. */
 int wfq_solve_qmr(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
                   const double *dirs, double E0, double rel_tol, int max_iter, int prec,
                   int refine_every, double *q, wfq_stats *stats, void *stream);

@@ -1182,7 +1182,7 @@ __global__ void k_qmr_restart_cols(int64_t na, const double2 *__restrict__ rnorm
 }
 
 template <class VT>
-static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
+static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *out) {
     Common cm;
     WFQ_TRY(cm.init(g, a, s));
     const int64_t n = cm.n, cc = cm.cc;
@@ -1209,12 +1209,28 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     WFQ_TRY(cm.select(act));
     WFQ_CUDA(cudaMemcpyAsync(cm.ra.ptr, cm.Ba.ptr, sizeof(double2) * n * cc, cudaMemcpyDeviceToDevice, s));
     WFQ_TRY(cm.colnorm(cm.ra.ptr, cc, cm.rnorm.ptr));
+    // mixed: restart at the latest after this many iterations, so that the stagnation test
+    // below sees every column regularly
+    const int cycle_cap = mixed ? (a.refine_every > 0 ? a.refine_every : 300) : INT32_MAX;
+    std::vector<double> prev_exact(cc, -1.0);
+    std::vector<int> flat(cc, 0), esc;
     for (;;) {
         WFQ_TRY(cm.classify(act, a.rel_tol, still));
-        // columns whose QMR broke down leave the active set
+        // columns whose QMR broke down leave the active set; a mixed solve hands them, and
+        // the columns that stalled over two restarts, to FP64 GMRES afterwards
         std::vector<int> keep;
-        for (int c : still)
+        for (int c : still) {
+            if (mixed && out) {
+                const bool slow = prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c];
+                flat[c] = slow ? flat[c] + 1 : 0;
+                prev_exact[c] = cm.res_h[c];
+                if (brk_h[c] || flat[c] >= STAGNATION_CYCLES) {
+                    esc.push_back(c);
+                    continue;
+                }
+            }
             if (!brk_h[c]) keep.push_back(c);
+        }
         if (keep.empty() || total >= a.max_iter) break;
         if (keep.size() != act.size()) WFQ_TRY(cm.narrow(act, keep));
         const int64_t na = (int64_t)act.size();
@@ -1266,7 +1282,7 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
             WFQ_CUDA(cudaMemcpyAsync(done_h.data(), done.ptr, sizeof(int) * na, cudaMemcpyDeviceToHost, s));
             WFQ_CUDA(cudaStreamSynchronize(s));
             if (std::all_of(done_h.begin(), done_h.end(), [](int v) { return v != 0; })) break;
-            if (mixed && a.refine_every > 0 && since >= a.refine_every) break;
+            if (since >= cycle_cap) break;
             WFQ_TRY(dmul(r.ptr, Dr.ptr));   // the one D product of the iteration
             k_colpart<VT><<<g1, 256, 0, s>>>(n, na, 1, RED_BILIN, r.ptr, 0, Dr.ptr, rs.cx, rs.ry, rs.nrb, cm.partial.ptr); note_launch();
             k_qmr_fin<<<gw, 256, 0, s>>>(na, rs.nrb, QF_RHO, cm.partial.ptr, q); note_launch();
@@ -1286,12 +1302,22 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         ++cycles;
         WFQ_TRY(cm.true_residual(a.q, na));
     }
+    if (out) {
+        std::sort(esc.begin(), esc.end());
+        out->escalate = esc;
+        out->res = cm.res_h;
+        out->iters = iters_h;
+        out->cycles = cycles;
+    }
     return finish_stats(a, cm, iters_h, cycles, brk_h);
 }
 
 int solve_qmr(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
-    if (a.prec == WFQ_PREC_MIXED) return qmr_impl<float2>(g, a, s);
-    return qmr_impl<double2>(g, a, s);
+    if (a.prec != WFQ_PREC_MIXED) return qmr_impl<double2>(g, a, s, nullptr);
+    GmresOut o1;
+    const int rc = qmr_impl<float2>(g, a, s, &o1);
+    if (o1.escalate.empty() || (rc != WFQ_OK && rc != WFQ_ENOCONV && rc != WFQ_EBREAKDOWN)) return rc;
+    return continue_columns(g, a, o1.escalate, o1.res, o1.iters, WFQ_PREC_FP64, 50, s);
 }
 
 }  // namespace wfq

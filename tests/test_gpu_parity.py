@@ -544,17 +544,22 @@ def test_cnt20k_full_size_mixed_block_gmres(W, ctx, orc, S):
 
 
 @pytest.mark.slow
-def test_gmres_mixed_low_frequency_large_flake_meets_bar(W, ctx, orc, S):
+@pytest.mark.parametrize("solver", ["gmres", "qmr"])
+def test_mixed_low_frequency_large_flake_meets_bar(W, ctx, orc, S, solver):
     """Low frequencies on a 15,000-atom flake with the field in plane: ||A|| ||q|| / ||R|| is
     large there, so the mixed refinement (double-float residuals) stalls just above the
-    1e-8 bar; such columns are finished by FP64 GMRES from the mixed iterate.  Every column
-    must meet the bar, re-measured by the oracle's operator, and the first column's alpha
-    must match the oracle's own FP64 GMRES solution to 1e-6."""
+    1e-8 bar; such columns are finished by FP64 GMRES from the mixed iterate (for mixed GMRES
+    and mixed QMR alike).  Every column must meet the bar, re-measured by the oracle's
+    operator, and the first column's alpha must match the oracle's own FP64 GMRES solution
+    to 1e-6."""
     xyz = S.honeycomb_flake(50)
     p = S.carbon_params(1.51)
     om = S.ev(np.array([0.0555, 0.067, 0.3]))
     g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 | W.STORE_BF16X2)
-    q, st, status = g.solve_gmres(om, [[1.0, 0, 0]], m=50, rel_tol=1e-8, max_iter=3000, prec=W.PREC_MIXED)
+    if solver == "gmres":
+        q, st, status = g.solve_gmres(om, [[1.0, 0, 0]], m=50, rel_tol=1e-8, max_iter=3000, prec=W.PREC_MIXED)
+    else:
+        q, st, status = g.solve_qmr(om, [[1.0, 0, 0]], rel_tol=1e-8, max_iter=3000, prec=W.PREC_MIXED)
     assert status == "WFQ_OK", st
     assert max(s["rel_residual"] for s in st) <= 1e-8
     csr = _oracle_csr(orc, xyz, p)
