@@ -32,9 +32,9 @@ namespace {
 
 inline unsigned nblk(int64_t total, int t = 256) { return (unsigned)((total + t - 1) / t); }
 
-// Threads per block of the one-thread-per-column FP64 kernels (Givens step, back
-// substitution): their work is a serial FP64 chain per column, and GB300 has only about two
-// FP64 FMAs per clock per SM, so the columns are spread over many SMs instead of filling one.
+// Threads per block of the one-thread-per-column Givens step: its work is a serial FP64
+// chain per column, and GB300 has only about two FP64 FMAs per clock per SM, so the columns
+// are spread over many SMs instead of filling one.
 constexpr int PER_COLUMN_BLOCK = 4;
 
 __device__ __forceinline__ double2 c_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -381,12 +381,29 @@ __device__ void shift_givens_col(const ShiftDev &st, int64_t c, int j, const dou
     const double2 *__restrict__ snv = st.sn + c;
     const double2 zc = st.z[c];
     double2 *__restrict__ R = st.Rt + (int64_t)j * (j + 1) / 2 * nc + c;
-    auto hv = [&](int i) { return h[i]; };
-    // t_i = h_i - z delta_ij, rotated by G_0 .. G_{j-1} (loads do not depend on the chain)
-    double2 prev = make_double2(hv(0) - (j == 0 ? zc.x : 0.0), j == 0 ? -zc.y : 0.0);
-#pragma unroll 4
-    for (int i = 0; i < j; ++i) {
-        const double2 nxt = make_double2(hv(i + 1) - (i + 1 == j ? zc.x : 0.0), i + 1 == j ? -zc.y : 0.0);
+    // t_i = h_i - z delta_ij, rotated by G_0 .. G_{j-1}.  The rotations' loads do not depend
+    // on the chain, so they are issued eight at a time ahead of it.
+    double2 prev = make_double2(h[0] - (j == 0 ? zc.x : 0.0), j == 0 ? -zc.y : 0.0);
+    int i = 0;
+    for (; i + 8 <= j; i += 8) {
+        double csr[8], hr[8];
+        double2 snr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            csr[u] = __ldg(csv + (int64_t)(i + u) * nc);
+            snr[u] = __ldg(snv + (int64_t)(i + u) * nc);
+            hr[u] = h[i + u + 1];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool diag = i + u + 1 == j;
+            const double2 nxt = make_double2(hr[u] - (diag ? zc.x : 0.0), diag ? -zc.y : 0.0);
+            R[(int64_t)(i + u) * nc] = c_add(c_scale(csr[u], prev), c_mul(snr[u], nxt));
+            prev = c_sub(c_scale(csr[u], nxt), c_conjmul(snr[u], prev));
+        }
+    }
+    for (; i < j; ++i) {
+        const double2 nxt = make_double2(h[i + 1] - (i + 1 == j ? zc.x : 0.0), i + 1 == j ? -zc.y : 0.0);
         const double cs = __ldg(csv + (int64_t)i * nc);
         const double2 sn = __ldg(snv + (int64_t)i * nc);
         R[(int64_t)i * nc] = c_add(c_scale(cs, prev), c_mul(sn, nxt));
@@ -430,29 +447,34 @@ __global__ void k_shift_givens(ShiftDev st, int j) {
     shift_givens_col(st, c, j, h, h[j + 1]);
 }
 
-// y = R^{-1} g over the column's jdone steps (columns still open use jlast + 1)
+// y = R^{-1} g over the column's jdone steps (columns still open use jlast + 1), a warp per
+// column, column-oriented: for k = jd-1 .. 0, y_k = y_k / R_kk, then y_l -= R_lk y_k for
+// l < k.  Column k of R is contiguous in the packed layout; lane l mod 32 owns y_l, and
+// the owner of y_k broadcasts it.
 __global__ void k_shift_backsolve(ShiftDev st, int jlast, double2 *__restrict__ y) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= st.ncols) return;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= st.ncols) return;   // whole warp
     const int64_t nc = st.ncols;
     const int jd = st.done[c] ? st.jdone[c] : jlast + 1;
-    st.jdone[c] = jd;
     const double2 *__restrict__ Rt = st.Rt + c;
     double2 *__restrict__ yc = y + c;
-    for (int l = jd - 1; l >= 0; --l) {
-        // four independent partial sums of R(l, k) y_k, k > l
-        double2 a0 = make_double2(0.0, 0.0), a1 = a0, a2 = a0, a3 = a0;
-        int k = l + 1;
-        for (; k + 3 < jd; k += 4) {
-            a0 = c_add(a0, c_mul(Rt[((int64_t)k * (k + 1) / 2 + l) * nc], yc[(int64_t)k * nc]));
-            a1 = c_add(a1, c_mul(Rt[((int64_t)(k + 1) * (k + 2) / 2 + l) * nc], yc[(int64_t)(k + 1) * nc]));
-            a2 = c_add(a2, c_mul(Rt[((int64_t)(k + 2) * (k + 3) / 2 + l) * nc], yc[(int64_t)(k + 2) * nc]));
-            a3 = c_add(a3, c_mul(Rt[((int64_t)(k + 3) * (k + 4) / 2 + l) * nc], yc[(int64_t)(k + 3) * nc]));
+    for (int l = lane; l < jd; l += 32) yc[(int64_t)l * nc] = st.g[(int64_t)l * nc + c];
+    for (int k = jd - 1; k >= 0; --k) {
+        const int owner = k & 31;
+        double2 yk = make_double2(0.0, 0.0);
+        if (lane == owner) {
+            yk = c_div(yc[(int64_t)k * nc], Rt[((int64_t)k * (k + 1) / 2 + k) * nc]);
+            yc[(int64_t)k * nc] = yk;
         }
-        for (; k < jd; ++k) a0 = c_add(a0, c_mul(Rt[((int64_t)k * (k + 1) / 2 + l) * nc], yc[(int64_t)k * nc]));
-        const double2 s = c_sub(st.g[(int64_t)l * nc + c], c_add(c_add(a0, a1), c_add(a2, a3)));
-        yc[(int64_t)l * nc] = c_div(s, Rt[((int64_t)l * (l + 1) / 2 + l) * nc]);
+        yk.x = __shfl_sync(0xffffffffu, yk.x, owner);
+        yk.y = __shfl_sync(0xffffffffu, yk.y, owner);
+        const int64_t col0 = (int64_t)k * (k + 1) / 2;
+        for (int l = lane; l < k; l += 32)
+            yc[(int64_t)l * nc] = c_sub(yc[(int64_t)l * nc], c_mul(Rt[(col0 + l) * nc], yk));
     }
+    __syncwarp();
+    if (lane == 0) st.jdone[c] = jd;
 }
 
 // q[i][c] = sum_{k < jdone_c} V_k[d_c][i] y[k][c]
@@ -708,7 +730,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         }
     }
     WFQ_TRY(dq.alloc(ctx, (size_t)n * nc, s));
-    k_shift_backsolve<<<nblk(nc, PER_COLUMN_BLOCK), PER_COLUMN_BLOCK, 0, s>>>(st, jlast, y.ptr); note_launch();
+    k_shift_backsolve<<<nblk(nc * 32, 128), 128, 0, s>>>(st, jlast, y.ptr); note_launch();
     k_shift_combine<<<nblk(n * nc), 256, 0, s>>>(n, nc, V.ptr, vstride, y.ptr, jdone.ptr, cdir.ptr, a.q); note_launch();
     k_shift_combine<<<nblk(n * nc), 256, 0, s>>>(n, nc, DV.ptr, vstride, y.ptr, jdone.ptr, cdir.ptr, dq.ptr); note_launch();
     WFQ_CUDA(cudaGetLastError());
