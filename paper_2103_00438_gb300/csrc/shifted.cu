@@ -54,14 +54,6 @@ __device__ __forceinline__ double2 c_div(double2 a, double2 b) {
 
 // ------------------------------------------------------------------ operator: A v (real)
 
-// x -> float pairs (hi = fp32(x), lo = fp32(x - hi))
-__global__ void k_split_real(int64_t total, const double *__restrict__ x, float *__restrict__ xh,
-                             float *__restrict__ xl) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    df_split(x[e], xh[e], xl[e]);
-}
-
 // Tilings of the double-float GEMV: rows per warp, 128-column load steps in flight per lane,
 // resident blocks per SM the register budget must allow.  The kernel is bound by
 // instruction issue of the double-float arithmetic (~12 FP32 instructions per entry and
@@ -197,32 +189,35 @@ void launch_dgemv_c(int cg, int tiling, int64_t n, int64_t ld, const float *Fh, 
 // directions d0 .. d0 + CG - 1.  One warp per row: the lanes stride over the row's
 // neighbours (coalesced CSR reads, each entry read once for all CG directions), then sum
 // in a fixed butterfly order.
-template <int CG>
+// LPR lanes per row (32 for long sodium rows, 8 for the ~50-entry carbon rows).
+template <int CG, int LPR>
 __global__ void __launch_bounds__(256) k_sparse_real(int64_t n, int d0, const int64_t *__restrict__ rowptr,
                                                      const int32_t *__restrict__ col, const double *__restrict__ val,
                                                      const double *__restrict__ U, double *__restrict__ W) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;   // whole warp
-    const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
+    const int lane = threadIdx.x & (LPR - 1);
+    const bool row_ok = i < n;   // rows past n still join the shuffles below
     double ui[CG], acc[CG];
 #pragma unroll
     for (int d = 0; d < CG; ++d) {
-        ui[d] = U[(int64_t)(d0 + d) * n + i];
+        ui[d] = row_ok ? U[(int64_t)(d0 + d) * n + i] : 0.0;
         acc[d] = 0.0;
     }
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
-        const double v = val[p];
-        const int64_t j = col[p];
+    if (row_ok) {
+        const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
+        for (int64_t p = p0 + lane; p < p1; p += LPR) {
+            const double v = val[p];
+            const int64_t j = col[p];
 #pragma unroll
-        for (int d = 0; d < CG; ++d) acc[d] += v * (U[(int64_t)(d0 + d) * n + j] - ui[d]);
+            for (int d = 0; d < CG; ++d) acc[d] += v * (U[(int64_t)(d0 + d) * n + j] - ui[d]);
+        }
     }
 #pragma unroll
     for (int d = 0; d < CG; ++d) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], off);
+        for (int off = LPR / 2; off > 0; off >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], off);
     }
-    if (lane == 0)
+    if (row_ok && lane == 0)
 #pragma unroll
         for (int d = 0; d < CG; ++d) W[(int64_t)(d0 + d) * n + i] = acc[d];
 }
@@ -332,13 +327,16 @@ __global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate(int64_t n, int C, in
     }
 }
 
-// v[d][i] = w[d][i] / hn[d]  (0 when hn = 0: the direction's Krylov space is exhausted)
+// v[d][i] = w[d][i] / hn[d] (0 when hn = 0: the direction's Krylov space is exhausted),
+// and v's float-pair split (xh, xl) for the next D product
 __global__ void k_rscale(int64_t n, int C, const double *__restrict__ hn, const double *__restrict__ w,
-                         double *__restrict__ v) {
+                         double *__restrict__ v, float *__restrict__ xh, float *__restrict__ xl) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n * C) return;
     const double h = hn[e / n];
-    v[e] = h > 0.0 ? w[e] / h : 0.0;
+    const double t = h > 0.0 ? w[e] / h : 0.0;
+    v[e] = t;
+    df_split(t, xh[e], xl[e]);
 }
 
 // ------------------------------------------------------------------ per-shift least squares
@@ -584,10 +582,8 @@ struct Arnoldi {
         return best;
     }
 
-    // u = D v for the C direction vectors v (double-float products)
-    int dmul(const double *v, double *u) {
-        k_split_real<<<nblk(n * C), 256, 0, s>>>(n * C, v, xh.ptr, xl.ptr);
-        note_launch();
+    // u = D v; xh / xl already hold v's float-pair split (written when v was normalised)
+    int dmul(double *u) {
         const double dbytes = 8.0 * (double)n * (double)(g->Dfh ? g->ldf : n);
         const bool pl = g->Dfh != nullptr;
         for (int d0 = 0; d0 < C; d0 += 4) {
@@ -607,14 +603,22 @@ struct Arnoldi {
     // w = (Kbar - P) u
     int sparse(const double *u, double *w) {
         KScope ks(g->ctx, WFQ_KT_SPARSE, s);
-        const unsigned blocks = nblk(n * 32);
+        const bool wide = g->nnz > 128 * n;   // long rows: a full warp per row
+        const unsigned blocks = nblk(n * (wide ? 32 : 8));
         for (int d0 = 0; d0 < C; d0 += 4) {
-            switch (std::min(4, C - d0)) {
-                case 1: k_sparse_real<1><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
-                case 2: k_sparse_real<2><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
-                case 3: k_sparse_real<3><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
-                default: k_sparse_real<4><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w); break;
+            const int cg = std::min(4, C - d0);
+#define WFQ_SP(CC)                                                                                   \
+    if (wide)                                                                                        \
+        k_sparse_real<CC, 32><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w);     \
+    else                                                                                             \
+        k_sparse_real<CC, 8><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w);
+            switch (cg) {
+                case 1: WFQ_SP(1) break;
+                case 2: WFQ_SP(2) break;
+                case 3: WFQ_SP(3) break;
+                default: WFQ_SP(4) break;
             }
+#undef WFQ_SP
             note_launch();
         }
         WFQ_CUDA(cudaGetLastError());
@@ -692,7 +696,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     WFQ_TRY(launch_rhs(g, (int)C, dirs.ptr, a.E0, R.ptr, s));
     k_take_rhs<<<nblk(n * C), 256, 0, s>>>(n, (int)C, R.ptr, ar.U.ptr); note_launch();
     WFQ_TRY(ar.dots(ar.U.ptr, 0, 1, ar.U.ptr, RF_NORM, m, -1, H.ptr, hn.ptr));
-    k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, ar.U.ptr, V.ptr); note_launch();
+    k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, ar.U.ptr, V.ptr, ar.xh.ptr, ar.xl.ptr); note_launch();
     std::vector<double> rn_h(C), tg(C);
     WFQ_CUDA(cudaMemcpyAsync(rn_h.data(), hn.ptr, sizeof(double) * C, cudaMemcpyDeviceToHost, s));
     WFQ_CUDA(cudaStreamSynchronize(s));   // also completes the cdir_h / om_h uploads
@@ -705,10 +709,9 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     std::vector<int> done_h(nc);
     int jlast = -1;
     for (int j = 0; j < m; ++j) {
-        const double *vj = V.ptr + (int64_t)j * vstride;
         double *dvj = DV.ptr + (int64_t)j * vstride;
         double *w = V.ptr + (int64_t)(j + 1) * vstride;
-        WFQ_TRY(ar.dmul(vj, dvj));
+        WFQ_TRY(ar.dmul(dvj));
         WFQ_TRY(ar.sparse(dvj, w));
         {
             KScope ko(ctx, WFQ_KT_ORTHO, s);
@@ -718,7 +721,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
                 note_launch();
             }
             WFQ_TRY(ar.dots(w, 0, 1, w, RF_NORM, m, j, H.ptr, hn.ptr));
-            k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, w, w); note_launch();
+            k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, w, w, ar.xh.ptr, ar.xl.ptr); note_launch();
             k_shift_givens<<<nblk(nc, PER_COLUMN_BLOCK), PER_COLUMN_BLOCK, 0, s>>>(st, j); note_launch();
             WFQ_CUDA(cudaGetLastError());
         }
