@@ -69,8 +69,8 @@ def parse():
 # sphere (FP64 D would be 180 GB); nothing stored for the 1M-atom disk (matrix-free).
 def store_for(name, wfq, solver="gmres"):
     if name == "sphere150k":
-        # the FP32 pair planes alone are 180 GB; the bf16 planes alone 90 GB
-        return wfq.STORE_F32X2 if solver == "shifted" else wfq.STORE_BF16X2
+        # the symmetric FP32 pair tiles are 90 GB, the bf16 planes 90 GB: both fit
+        return wfq.STORE_F32X2_SYM | wfq.STORE_BF16X2
     if name in ("disk1m", "disk100k"):
         return 0
     return wfq.STORE_FP64 | wfq.STORE_BF16X2 | wfq.STORE_F32X2
@@ -79,6 +79,9 @@ def store_for(name, wfq, solver="gmres"):
 # DRAM bytes per stored D entry that ncu measured for one k_dgemv_df launch (cnt8k, N = 8200:
 # 543.5 MB read + written for 8200 x 8200 entries of the FP32 pair planes).
 DGEMV_DRAM_BYTES_PER_ENTRY = 543.5e6 / (8200.0 * 8200.0)
+
+# FP32 lane-instructions per second of the whole GPU: 152 SMs x 128 lanes x 2070 MHz.
+FP32_LANE_OPS_PER_S = 152 * 128 * 2.07e9
 
 # Minimum FP32-pipe instructions to generate one D entry as a bf16 hi/lo pair on the
 # matrix-free path: 3 coordinate differences, 3 for r^2, 1 for sigma^2, 1 far/near test,
@@ -336,7 +339,22 @@ def run_ours(args, rank, world, dist):
     # columns converge): 6 N^2 C tensor flops (three bf16 products of 2 N^2 C each).
     peaks, peak_src = load_peaks()
     roof = None
-    if gv_n and gv_ms >= gemm_ms:
+    if gv_n and gv_ms >= gemm_ms and store & wfq.STORE_F32X2_SYM and not store & wfq.STORE_F32X2:
+        # shifted solver on the symmetric tiles: half of D streamed, each tile used for two
+        # products, so the double-float arithmetic bounds it: 12 FP32-pipe instructions per
+        # (entry, vector) product, N^2 x ndir products per launch
+        avg_s = gv_ms / gv_n * 1e-3
+        achieved = 12.0 * n * n * nd / avg_s / 1e12
+        peak = FP32_LANE_OPS_PER_S / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FP32 Tinst/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_dsymv_df + k_dsymv_finish (symmetric double-float D product)", "launches": gv_n,
+                "avg_ms": gv_ms / gv_n, "bytes_per_launch": gv_bytes / gv_n,
+                "hbm_achieved_gbs": gv_bytes / gv_n / avg_s / 1e9,
+                "hbm_frac": gv_bytes / gv_n / avg_s / 1e9 / peaks["hbm_gbs"],
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (one FP32 instruction per lane "
+                               "per clock); work: 12 instructions per double-float multiply-add"}
+    elif gv_n and gv_ms >= gemm_ms:
         # shifted solver: the dominant kernel streams D (FP32 pair planes) once per launch
         achieved_gbs = gv_bytes / (gv_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]

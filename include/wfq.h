@@ -84,6 +84,15 @@ typedef struct {
                                 4: double-float products on the FP32 pipes without FP64
                                 arithmetic (the shifted solver's operator, the refinement
                                 residual) */
+#define WFQ_STORE_F32X2_SYM 8u  /* the same FP32 hi + lo pairs for the upper triangle only
+                                (D is symmetric, Eq. 3): 64 x 64 tiles (I, J), I <= J, each
+                                stored row-major as 4096 hi then 4096 lo floats, tiles in
+                                row order (diagonal tiles in full, zero beyond N):
+                                T (T + 1) / 2 * 32 KiB with T = ceil(N / 64), about half of
+                                WFQ_STORE_F32X2.  The shifted solver's D product uses it
+                                when the full planes are not stored, each tile serving
+                                both D_IJ x_J and D_IJ^T x_I (about the same time, half
+                                the memory). */
 
 /* Arithmetic of an apply / of the inner Krylov iterations. */
 enum {

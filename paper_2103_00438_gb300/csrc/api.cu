@@ -142,7 +142,8 @@ static int galloc(wfq_geom *g, T **p, size_t count) {
 
 static void free_geom(wfq_geom *g) {
     void *ptrs[] = {g->xyz, g->atom64, g->atom32, g->atomdf, g->eta, g->rowptr, g->col,
-                    g->val64, g->val32, g->D64, g->Dhi, g->Dlo, g->Dfh, g->Dfl};
+                    g->val64, g->val32, g->D64, g->Dhi, g->Dlo, g->Dfh, g->Dfl,
+                    g->Dsym, g->sym_items, g->sym_item_start};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -290,7 +291,8 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     *out = nullptr;
     if (n < 1) return fail(WFQ_EINVAL, "n must be >= 1");
     if (!xyz) return fail(WFQ_EINVAL, "xyz is NULL");
-    if (store & ~(WFQ_STORE_FP64 | WFQ_STORE_BF16X2 | WFQ_STORE_F32X2)) return fail(WFQ_EINVAL, "unknown storage flag");
+    if (store & ~(WFQ_STORE_FP64 | WFQ_STORE_BF16X2 | WFQ_STORE_F32X2 | WFQ_STORE_F32X2_SYM))
+        return fail(WFQ_EINVAL, "unknown storage flag");
     WFQ_TRY(check_params(p));
     if (!finite_all(xyz, 3 * n)) return fail(WFQ_EINVAL, "xyz has a non-finite entry");
     std::vector<double> eta_h(n, p->eta);
@@ -364,6 +366,25 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
         if ((rc = galloc(g, &g->Dfh, (size_t)n * g->ldf))) return bail(rc);
         if ((rc = galloc(g, &g->Dfl, (size_t)n * g->ldf))) return bail(rc);
     }
+    std::vector<SymItem> sym_items;
+    std::vector<int> sym_start;
+    if (store & WFQ_STORE_F32X2_SYM) {
+        // work items of the symmetric product: each tile row split into runs of at most
+        // kSymChunk tiles (balances the triangle's long and short rows)
+        const int64_t T = (n + kSymTile - 1) / kSymTile;
+        const int kSymChunk = 16;
+        g->sym_nt = T;
+        for (int64_t I = 0; I < T; ++I) {
+            sym_start.push_back((int)sym_items.size());
+            for (int64_t J0 = I; J0 < T; J0 += kSymChunk)
+                sym_items.push_back(SymItem{(int)I, (int)J0, (int)std::min<int64_t>(J0 + kSymChunk, T), 0});
+        }
+        sym_start.push_back((int)sym_items.size());
+        g->sym_nitems = (int64_t)sym_items.size();
+        if ((rc = galloc(g, &g->Dsym, (size_t)(T * (T + 1) / 2) * 2 * kSymTile * kSymTile))) return bail(rc);
+        if ((rc = galloc(g, &g->sym_items, sym_items.size()))) return bail(rc);
+        if ((rc = galloc(g, &g->sym_item_start, sym_start.size()))) return bail(rc);
+    }
     auto up = [&](void *dst, const void *src, size_t bytes) -> int {
         if (bytes == 0) return WFQ_OK;
         cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -379,6 +400,10 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     if ((rc = up(g->col, col.data(), sizeof(int32_t) * g->nnz))) return bail(rc);
     if ((rc = up(g->val64, val.data(), sizeof(double) * g->nnz))) return bail(rc);
     if ((rc = up(g->val32, val32.data(), sizeof(float) * g->nnz))) return bail(rc);
+    if (!sym_items.empty()) {
+        if ((rc = up(g->sym_items, sym_items.data(), sizeof(SymItem) * sym_items.size()))) return bail(rc);
+        if ((rc = up(g->sym_item_start, sym_start.data(), sizeof(int) * sym_start.size()))) return bail(rc);
+    }
     if ((rc = launch_build_d(g, nullptr))) return bail(rc);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return bail(fail(WFQ_ECUDA, std::string("D build: ") + cudaGetErrorString(e)));

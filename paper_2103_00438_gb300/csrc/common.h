@@ -54,6 +54,15 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // to a multiple of kTilePad with zero entries.
 constexpr int64_t kTilePad = 128;
 
+// Symmetric tiled D (WFQ_STORE_F32X2_SYM): edge of a tile, and the work item of one CTA of
+// the symmetric product -- tiles J0 .. J1 - 1 of tile row I.
+constexpr int64_t kSymTile = 64;
+struct SymItem {
+    int I, J0, J1, pad;
+};
+// index of tile (I, J), I <= J, in the row-ordered upper triangle of T x T tiles
+__host__ __device__ inline int64_t sym_tile(int64_t I, int64_t J, int64_t T) { return I * T - I * (I - 1) / 2 + (J - I); }
+
 // Per-atom record for the FP64 kernels: position and Gaussian width (Eq. 4).
 struct __align__(32) atom64_t {
     double x, y, z, w;
@@ -122,6 +131,12 @@ struct wfq_geom {
     float *Dfh = nullptr;       // n x ldf row-major: fl32(D_ij) (zero for j >= n)
     float *Dfl = nullptr;       // n x ldf row-major: fl32(D_ij - Dfh_ij)
     int64_t ldf = 0;            // n rounded up to 4 (16-byte rows)
+    // upper-triangle 64 x 64 tiles of the FP32 pairs (WFQ_STORE_F32X2_SYM)
+    float *Dsym = nullptr;      // tile t(I, J): 4096 hi then 4096 lo floats, row-major
+    int64_t sym_nt = 0;         // tiles per side, ceil(n / 64)
+    wfq::SymItem *sym_items = nullptr;   // work items of the symmetric product (device)
+    int64_t sym_nitems = 0;
+    int *sym_item_start = nullptr;       // [sym_nt + 1]: first item of each tile row (device)
 };
 
 namespace wfq {

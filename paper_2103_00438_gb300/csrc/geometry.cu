@@ -154,7 +154,31 @@ __global__ void k_build_d(const atom64_t *__restrict__ atom, const double *__res
     }
 }
 
+// Upper-triangle tiles of the FP32 pair D: block (x, y) fills 256 entries of tile row
+// I = y; entry q of the row's run of tiles is tile J = I + q / 4096, element q % 4096.
+__global__ void k_build_dsym(const atom64_t *__restrict__ atom, const double *__restrict__ eta, int64_t n,
+                             int64_t T, float *__restrict__ Dsym) {
+    const int64_t I = blockIdx.y;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t J = I + q / (kSymTile * kSymTile);
+    if (J >= T) return;
+    const int64_t e = q % (kSymTile * kSymTile);
+    const int64_t i = I * kSymTile + e / kSymTile, j = J * kSymTile + e % kSymTile;
+    const double v = (i < n && j < n) ? d_entry64(atom[i], atom[j], eta[i], i == j) : 0.0;
+    float *tile = Dsym + sym_tile(I, J, T) * 2 * kSymTile * kSymTile;
+    const float h = (float)v;
+    tile[e] = h;
+    tile[kSymTile * kSymTile + e] = (float)(v - (double)h);
+}
+
 int launch_build_d(const wfq_geom *g, cudaStream_t s) {
+    if (g->Dsym) {
+        const int64_t T = g->sym_nt;
+        if (T > 65535) return fail(WFQ_EUNSUPPORTED, "symmetric tiled D with more than 65535 tile rows");
+        dim3 grid((unsigned)((T * kSymTile * kSymTile + 255) / 256), (unsigned)T);
+        k_build_dsym<<<grid, 256, 0, s>>>(g->atom64, g->eta, g->n, T, g->Dsym); note_launch();
+        WFQ_CUDA(cudaGetLastError());
+    }
     if (!g->D64 && !g->Dhi && !g->Dfh) return WFQ_OK;
     const int64_t lim = g->Dhi ? g->npad : (g->Dfh ? g->ldf : g->n);   // ldf <= npad
     dim3 block(64, 4);

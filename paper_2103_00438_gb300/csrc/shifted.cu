@@ -162,6 +162,133 @@ __global__ void __launch_bounds__(GV_WARPS * 32, MINB) k_dgemv_df(int64_t n, int
     }
 }
 
+// ---- the same product from the symmetric tiled storage (upper-triangle 64 x 64 tiles):
+// every stored tile (I, J), I < J, serves both U_I += D_IJ x_J and U_J += D_IJ^T x_I, so D is
+// read once for the triangle instead of the full matrix -- half the memory; the time is
+// that of the full-plane product (both are bound by issue of the double-float arithmetic:
+// 0.76 vs 0.74 ms at N = 20000).  One CTA per work item (tiles J0 ..
+// J1 - 1 of tile row I); thread (tr, tc) of the 16 x 16 grid owns a 4 x 4 sub-block of each
+// tile.  Row sums accumulate over the item in registers; the column sums of a tile are
+// reduced over the 16 thread rows in shared memory.  Both go out as float pairs (rowpart per
+// item, colpart per tile) and k_dsymv_finish adds them up in a fixed order.  The diagonal
+// tile, stored in full, contributes only row sums.
+constexpr int SY_T = (int)kSymTile;
+
+template <int C>
+__global__ void __launch_bounds__(256, 2) k_dsymv_df(int64_t n, int64_t T, const float *__restrict__ Dsym,
+                                                     const SymItem *__restrict__ items,
+                                                     const float *__restrict__ xh, const float *__restrict__ xl,
+                                                     float2 *__restrict__ rowpart, float2 *__restrict__ colpart) {
+    __shared__ __align__(16) float sxh[C][SY_T];
+    __shared__ __align__(16) float sxl[C][SY_T];
+    __shared__ float2 cred[16][SY_T * C];
+    const SymItem it = items[blockIdx.x];
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    const int64_t I = it.I;
+    float xih[4][C], xil[4][C], rh[4][C], rl[4][C];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = I * SY_T + tr * 4 + r;
+#pragma unroll
+        for (int d = 0; d < C; ++d) {
+            xih[r][d] = i < n ? xh[(int64_t)d * n + i] : 0.f;
+            xil[r][d] = i < n ? xl[(int64_t)d * n + i] : 0.f;
+            rh[r][d] = rl[r][d] = 0.f;
+        }
+    }
+    for (int J = it.J0; J < it.J1; ++J) {
+        const int64_t t = sym_tile(I, J, T);
+        const float *th = Dsym + t * 2 * SY_T * SY_T, *tl = th + SY_T * SY_T;
+        __syncthreads();   // the previous tile's shared-memory readers are done
+        if (tid < C * SY_T) {
+            const int d = tid / SY_T, c = tid % SY_T;
+            const int64_t j = (int64_t)J * SY_T + c;
+            sxh[d][c] = j < n ? xh[(int64_t)d * n + j] : 0.f;
+            sxl[d][c] = j < n ? xl[(int64_t)d * n + j] : 0.f;
+        }
+        float4 dh[4], dl[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            dh[r] = __ldg(reinterpret_cast<const float4 *>(th + (tr * 4 + r) * SY_T + tc * 4));
+            dl[r] = __ldg(reinterpret_cast<const float4 *>(tl + (tr * 4 + r) * SY_T + tc * 4));
+        }
+        __syncthreads();
+        const bool diag = J == I;
+        float ch[4][C], cl[4][C];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int d = 0; d < C; ++d) ch[c][d] = cl[c][d] = 0.f;
+#pragma unroll
+        for (int d = 0; d < C; ++d) {
+            const float4 ah = *reinterpret_cast<const float4 *>(&sxh[d][tc * 4]);
+            const float4 al = *reinterpret_cast<const float4 *>(&sxl[d][tc * 4]);
+            const float xjh[4] = {ah.x, ah.y, ah.z, ah.w}, xjl[4] = {al.x, al.y, al.z, al.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float vh[4] = {dh[r].x, dh[r].y, dh[r].z, dh[r].w};
+                const float vl[4] = {dl[r].x, dl[r].y, dl[r].z, dl[r].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    df_mac(vh[c], vl[c], xjh[c], xjl[c], rh[r][d], rl[r][d]);
+                    if (!diag) df_mac(vh[c], vl[c], xih[r][d], xil[r][d], ch[c][d], cl[c][d]);
+                }
+            }
+        }
+        if (!diag) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int d = 0; d < C; ++d) cred[tr][(tc * 4 + c) * C + d] = make_float2(ch[c][d], cl[c][d]);
+            __syncthreads();
+            if (tid < SY_T * C) {
+                float sh = 0.f, sl = 0.f;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) df_add(sh, sl, cred[q][tid].x, cred[q][tid].y);
+                colpart[t * SY_T * C + tid] = make_float2(sh, sl);   // (column, direction) = (tid / C, tid % C)
+            }
+        }
+    }
+    // row sums over the 16 threads of a thread row (16 consecutive lanes), fixed butterfly
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int d = 0; d < C; ++d)
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, rh[r][d], off);
+                const float ol = __shfl_xor_sync(0xffffffffu, rl[r][d], off);
+                df_add(rh[r][d], rl[r][d], oh, ol);
+            }
+    if (tc == 0)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int d = 0; d < C; ++d)
+                rowpart[((int64_t)blockIdx.x * SY_T + tr * 4 + r) * C + d] = make_float2(rh[r][d], rl[r][d]);
+}
+
+// U[d][i] = (row sums of the items of tile row K) + (column sums of tiles (I, K), I < K),
+// K = i / 64, added in that fixed order in double-float.
+__global__ void k_dsymv_finish(int64_t n, int C, int64_t T, const int *__restrict__ item_start,
+                               const float2 *__restrict__ rowpart, const float2 *__restrict__ colpart,
+                               double *__restrict__ U) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * C) return;
+    const int d = (int)(e / n);
+    const int64_t i = e - (int64_t)d * n, K = i / SY_T, r = i % SY_T;
+    float sh = 0.f, sl = 0.f;
+    for (int q = item_start[K]; q < item_start[K + 1]; ++q) {
+        const float2 v = rowpart[((int64_t)q * SY_T + r) * C + d];
+        df_add(sh, sl, v.x, v.y);
+    }
+    for (int64_t I = 0; I < K; ++I) {
+        const float2 v = colpart[(sym_tile(I, K, T) * SY_T + r) * C + d];
+        df_add(sh, sl, v.x, v.y);
+    }
+    U[e] = (double)sh + (double)sl;
+}
+
 template <int C, bool PL>
 void launch_dgemv(int tiling, int64_t n, int64_t ld, const float *Fh, const float *Fl, const double *D64,
                   const float *xh, const float *xl, double *U, cudaStream_t s) {
@@ -523,6 +650,7 @@ struct Arnoldi {
     int nrb;
     DevBuf<float> xh, xl;
     DevBuf<double> U, partial, coef;
+    DevBuf<float2> rowpart, colpart;   // symmetric product partial sums
 
     int init(wfq_geom *geom, int ndir, int m, cudaStream_t stream) {
         g = geom;
@@ -536,6 +664,11 @@ struct Arnoldi {
         WFQ_TRY(U.alloc(g->ctx, (size_t)n * C, s));
         WFQ_TRY(partial.alloc(g->ctx, (size_t)nrb * (m + 1) * C, s));
         WFQ_TRY(coef.alloc(g->ctx, (size_t)(m + 1) * C, s));
+        if (g->Dsym && !g->Dfh) {
+            const int64_t T = g->sym_nt, cg = std::min<int64_t>(C, 4);
+            WFQ_TRY(rowpart.alloc(g->ctx, (size_t)g->sym_nitems * kSymTile * cg, s));
+            WFQ_TRY(colpart.alloc(g->ctx, (size_t)(T * (T + 1) / 2) * kSymTile * cg, s));
+        }
         return WFQ_OK;
     }
 
@@ -584,6 +717,29 @@ struct Arnoldi {
 
     // u = D v; xh / xl already hold v's float-pair split (written when v was normalised)
     int dmul(double *u) {
+        if (g->Dsym && !g->Dfh) {   // symmetric tiles: half the bytes, each tile used twice (the
+                                    // full planes, when also stored, measured slightly faster)
+            const int64_t T = g->sym_nt;
+            const double dbytes = (double)(T * (T + 1) / 2) * 2.0 * kSymTile * kSymTile * 4.0;
+            for (int d0 = 0; d0 < C; d0 += 4) {
+                const int cg = std::min(4, C - d0);
+                const float *ph = xh.ptr + (int64_t)d0 * n, *pxl = xl.ptr + (int64_t)d0 * n;
+                KScope ks(g->ctx, WFQ_KT_DGEMV_DF, s, dbytes);
+                const unsigned items = (unsigned)g->sym_nitems;
+                switch (cg) {
+                    case 1: k_dsymv_df<1><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rowpart.ptr, colpart.ptr); break;
+                    case 2: k_dsymv_df<2><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rowpart.ptr, colpart.ptr); break;
+                    case 3: k_dsymv_df<3><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rowpart.ptr, colpart.ptr); break;
+                    default: k_dsymv_df<4><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rowpart.ptr, colpart.ptr); break;
+                }
+                note_launch();
+                k_dsymv_finish<<<nblk(n * cg), 256, 0, s>>>(n, cg, T, g->sym_item_start, rowpart.ptr, colpart.ptr,
+                                                           u + (int64_t)d0 * n);
+                note_launch();
+            }
+            WFQ_CUDA(cudaGetLastError());
+            return WFQ_OK;
+        }
         const double dbytes = 8.0 * (double)n * (double)(g->Dfh ? g->ldf : n);
         const bool pl = g->Dfh != nullptr;
         for (int d0 = 0; d0 < C; d0 += 4) {
@@ -647,8 +803,9 @@ size_t shifted_footprint(const wfq_geom *g, int64_t ncols, int ndir, int m) {
 }
 
 int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
-    if (!g->Dfh && !g->D64)
-        return fail(WFQ_EUNSUPPORTED, "shifted GMRES needs a stored D (WFQ_STORE_F32X2 or WFQ_STORE_FP64)");
+    if (!g->Dsym && !g->Dfh && !g->D64)
+        return fail(WFQ_EUNSUPPORTED,
+                    "shifted GMRES needs a stored D (WFQ_STORE_F32X2_SYM, WFQ_STORE_F32X2 or WFQ_STORE_FP64)");
     wfq_ctx *ctx = g->ctx;
     const int64_t n = g->n, C = a.ndir, nc = a.col_omega ? a.ncols : a.nfreq * C;
     int m = a.m > 0 ? a.m : 600;

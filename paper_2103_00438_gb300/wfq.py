@@ -16,7 +16,7 @@ from . import build as _build
 WFQ_OK = 0
 STATUS = {0: "WFQ_OK", -1: "WFQ_EINVAL", -2: "WFQ_ESINGULAR", -3: "WFQ_ENOMEM", -4: "WFQ_ENOCONV",
           -5: "WFQ_EBREAKDOWN", -6: "WFQ_ETIMEOUT", -7: "WFQ_ECUDA", -8: "WFQ_EUNSUPPORTED"}
-STORE_FP64, STORE_BF16X2, STORE_F32X2 = 1, 2, 4
+STORE_FP64, STORE_BF16X2, STORE_F32X2, STORE_F32X2_SYM = 1, 2, 4, 8
 PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2
 
 # every symbol include/wfq.h declares

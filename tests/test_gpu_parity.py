@@ -342,13 +342,16 @@ def test_batched_columns_each_match_oracle(W, ctx, orc, S):
 
 # ----------------------------------------------------------------------------- shifted GMRES
 
-def test_shifted_gmres_iterates_match_oracle_gmres(W, ctx, orc, S):
+@pytest.mark.parametrize("store", ["f32x2", "f32x2sym"])
+def test_shifted_gmres_iterates_match_oracle_gmres(W, ctx, orc, S, store):
     """After k Arnoldi steps every (omega, direction) column of the shifted solver holds
     the k-step unrestarted GMRES iterate of its own system (A - z(omega) I) q = R_dir:
-    the Krylov space of A - zI from R does not depend on z."""
+    the Krylov space of A - zI from R does not depend on z.  D from the full FP32 pair
+    planes or from the symmetric upper-triangle tiles (216 atoms: 4 tile rows, a ragged
+    last tile)."""
     xyz = S.honeycomb_flake(6)
     p = _carbon(S)
-    g = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2 if store == "f32x2" else W.STORE_F32X2_SYM)
     sysm = orc.System(xyz, p)
     om = S.ev([0.3, 0.7, 1.4])
     dirs = np.array([[1.0, 0, 0], [0, 1.0, 0]])
@@ -365,14 +368,14 @@ def test_shifted_gmres_iterates_match_oracle_gmres(W, ctx, orc, S):
                 assert np.linalg.norm(q[:, c] - qo) <= 1e-10 * np.linalg.norm(qo), (k, f, d)
 
 
-@pytest.mark.parametrize("store", ["f32x2", "fp64"])
+@pytest.mark.parametrize("store", ["f32x2", "fp64", "f32x2sym"])
 def test_shifted_gmres_columns_match_lu(W, ctx, orc, S, store):
     """All frequencies x directions from the shared real Arnoldi processes; each column's
     alpha equals its own oracle LU solve and its FP64 residual meets the tolerance without
     any block-GMRES continuation."""
     xyz = S.nanotube(5, 5, 30)          # 600 atoms, axis z
     p = S.carbon_params(1.04)
-    flag = W.STORE_F32X2 if store == "f32x2" else W.STORE_FP64
+    flag = {"f32x2": W.STORE_F32X2, "fp64": W.STORE_FP64, "f32x2sym": W.STORE_F32X2_SYM}[store]
     g = W.Geometry(ctx, xyz, p, store=flag)
     sysm = orc.System(xyz, p)
     om = S.ev([0.15, 0.6, 1.1, 1.9])
@@ -446,6 +449,23 @@ def test_shifted_gmres_bitwise_repeatable_across_contexts(W, S):
         g.close()
         c.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_shifted_gmres_symmetric_tiles_equal_full_planes(W, ctx, S):
+    """The symmetric tiled D (each stored tile used for D_IJ x_J and D_IJ^T x_I) gives the
+    same solves as the full FP32 pair planes up to double-float rounding: 3000 atoms, 47 tile
+    rows (a ragged last tile), several work items per tile row."""
+    xyz = S.random_cluster(3000, seed=9)
+    p = _carbon(S, r0=2.7)
+    om = S.ev([0.35, 1.1])
+    ga = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2)
+    gb = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2_SYM)
+    qa, sa, st_a = ga.solve_gmres_shifted(om, np.eye(3), rel_tol=1e-10, prec=W.PREC_FP64)
+    qb, sb, st_b = gb.solve_gmres_shifted(om, np.eye(3), rel_tol=1e-10, prec=W.PREC_FP64)
+    assert st_a == "WFQ_OK" and st_b == "WFQ_OK"
+    assert [s["iters"] for s in sa] == [s["iters"] for s in sb]
+    assert np.linalg.norm(qa - qb) <= 1e-10 * np.linalg.norm(qa)
+    assert max(s["rel_residual"] for s in sb) <= 1e-10
 
 
 def test_shifted_gmres_needs_stored_d(W, ctx, S):
