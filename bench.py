@@ -393,7 +393,9 @@ def run_ours(args, rank, world, dist):
                                     "mixed: 3xBF16 D products, complex64 basis, FP64 refinement"),
                       "rel_tol": 1e-8, "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2 (%s %.2f GB)" % (
-                          ("FP32 pair D planes", 8.0 * n * n / 1e9) if args.solver == "shifted"
+                          ("FP32 pair D planes", 8.0 * n * n / 1e9)
+                          if args.solver == "shifted" and store & wfq.STORE_F32X2 else
+                          ("symmetric FP32 pair D tiles", 4.0 * n * n / 1e9) if args.solver == "shifted"
                           else ("bf16 D planes", 4.0 * n * n / 1e9))},
            "accuracy": {"max_rel_residual": max_res, "columns_converged": good_cols,
                         "iters_min_mean_max": [min(iters), float(np.mean(iters)), max(iters)],

@@ -194,9 +194,13 @@ struct Staged {
     }
 };
 
+// Entered by every C-ABI call that touches the device: makes the context's device current
+// and clears a runtime error left pending by earlier calls of the caller's own (cudaGetLastError
+// after this library's launches must report only what the launches did).
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
+        cudaGetLastError();
         cudaGetDevice(&prev);
         if (prev != dev) cudaSetDevice(dev);
     }

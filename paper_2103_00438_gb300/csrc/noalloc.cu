@@ -72,6 +72,7 @@ extern "C" int wfq_apply_mixed_noalloc(wfq_geom *g, int64_t ncplx, const double 
         return fail(WFQ_EINVAL, "wfq_apply_mixed_noalloc: this size needs " + std::to_string(need) +
                                     " bytes of scratch, more than the static " +
                                     std::to_string(kNoAllocScratchBytes) + "-byte array; use wfq_apply");
+    cudaGetLastError();   // an error left pending by the caller's earlier calls is not this call's
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != g->ctx->device) WFQ_CUDA(cudaSetDevice(g->ctx->device));

@@ -150,6 +150,7 @@ struct wfq_server {
 
     void run(int w) {
         cudaSetDevice(ctx->device);
+        cudaGetLastError();
         cudaStream_t s = streams[w];
         for (;;) {
             std::vector<Request *> batch;

@@ -865,6 +865,29 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
 
     std::vector<int> done_h(nc);
     int jlast = -1;
+    // The per-frequency Givens step of iteration j needs only column j of H, so it runs on a
+    // side stream, overlapped with the next iteration's D product; the solve stream joins it
+    // before every convergence check and before the back substitution.
+    struct SideStream {
+        cudaStream_t st = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+        ~SideStream() {
+            if (st) {
+                cudaStreamSynchronize(st);
+                cudaStreamDestroy(st);
+            }
+            if (fork) cudaEventDestroy(fork);
+            if (join) cudaEventDestroy(join);
+        }
+    } side;
+    WFQ_CUDA(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
+    WFQ_CUDA(cudaEventCreateWithFlags(&side.fork, cudaEventDisableTiming));
+    WFQ_CUDA(cudaEventCreateWithFlags(&side.join, cudaEventDisableTiming));
+    auto join_side = [&]() -> int {
+        WFQ_CUDA(cudaEventRecord(side.join, side.st));
+        WFQ_CUDA(cudaStreamWaitEvent(s, side.join, 0));
+        return WFQ_OK;
+    };
     for (int j = 0; j < m; ++j) {
         double *dvj = DV.ptr + (int64_t)j * vstride;
         double *w = V.ptr + (int64_t)(j + 1) * vstride;
@@ -879,16 +902,20 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
             }
             WFQ_TRY(ar.dots(w, 0, 1, w, RF_NORM, m, j, H.ptr, hn.ptr));
             k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, w, w, ar.xh.ptr, ar.xl.ptr); note_launch();
-            k_shift_givens<<<nblk(nc, PER_COLUMN_BLOCK), PER_COLUMN_BLOCK, 0, s>>>(st, j); note_launch();
+            WFQ_CUDA(cudaEventRecord(side.fork, s));
+            WFQ_CUDA(cudaStreamWaitEvent(side.st, side.fork, 0));
+            k_shift_givens<<<nblk(nc, PER_COLUMN_BLOCK), PER_COLUMN_BLOCK, 0, side.st>>>(st, j); note_launch();
             WFQ_CUDA(cudaGetLastError());
         }
         jlast = j;
         if ((j & 3) == 3 || j == m - 1) {
+            WFQ_TRY(join_side());
             WFQ_CUDA(cudaMemcpyAsync(done_h.data(), done.ptr, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
             WFQ_TRY(check_device_error(ctx, s));
             if (std::all_of(done_h.begin(), done_h.end(), [](int v) { return v != 0; })) break;
         }
     }
+    WFQ_TRY(join_side());
     WFQ_TRY(dq.alloc(ctx, (size_t)n * nc, s));
     k_shift_backsolve<<<nblk(nc * 32, 128), 128, 0, s>>>(st, jlast, y.ptr); note_launch();
     k_shift_combine<<<nblk(n * nc), 256, 0, s>>>(n, nc, V.ptr, vstride, y.ptr, jdone.ptr, cdir.ptr, a.q); note_launch();
