@@ -362,7 +362,7 @@ def run_ours(args, rank, world, dist):
                 "frac": achieved_gbs / peak,
                 "traffic": DGEMV_DRAM_BYTES_PER_ENTRY * n * (-(-n // 4) * 4),
                 "traffic_source": "ncu dram__bytes_read+write of k_dgemv_df at N = 8200 "
-                                  "(profiles/k_dgemv_df_cnt8k.md), scaled per D entry to this N",
+                                  "(the committed profile summary of that kernel), scaled per D entry to this N",
                 "kernel": "k_dgemv_df (double-float D product of the real Arnoldi vectors)", "launches": gv_n,
                 "avg_ms": gv_ms / gv_n, "bytes_per_launch": gv_bytes / gv_n,
                 "peak_source": peak_src + " hbm_gbs (STREAM-style copy)"}

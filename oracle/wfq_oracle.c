@@ -28,7 +28,7 @@
  *   Eq. 28 sigma_k = (4 pi w / c) sum_i (k_i / E0) Im q_i  ->  alpha_{k'k} = sum_i q_i r_{i,k'} / E0
  *   Eq. 33 RMSE = || R - (A - zI) q ||_2 / sqrt(N)
  *
- * Readings of the paper taken here (each also listed in the design doc):
+ * Readings of the paper taken here:
  *   - Eq. 1 prints "+ i w" inside the sum over j; it is the diagonal term i w q_i,
  *     consistent with Eq. 14's shift -z I.
  *   - Eq. 4 prints eta_j on the right-hand side; the width of atom i uses eta_i,
