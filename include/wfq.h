@@ -234,8 +234,12 @@ int wfq_rhs(wfq_geom *g, int ndir, const double *dirs, double E0, double *R, voi
  *   max_iter: cap on Krylov iterations per column.
  *   prec: WFQ_PREC_FP64 -- FP64 operator and complex128 Krylov basis;
  *         WFQ_PREC_MIXED -- each restart cycle iterates with the mixed operator and a
- *         complex64 basis (FP64 inner products, norms and Givens rotations); every cycle
- *         starts from the FP64 true residual (iterative refinement).
+ *         complex64 basis (FP64-grade inner products, FP64 norms and Givens rotations);
+ *         a cycle starts from the true residual at FP64 accuracy (iterative refinement)
+ *         -- or, while every column is still above 1e-3 ||R||, from the mixed-operator
+ *         residual; a column whose true residual shrank by less than 2x in each of two
+ *         consecutive cycles is finished by plain FP64 GMRES(m) from its iterate.
+ *         Convergence is always decided on the FP64-accuracy true residual.
  * q: output, N x ncols complex128 atom-major.  stats: host array of ncols, or NULL.
  * Returns WFQ_OK when every column converged, WFQ_ENOCONV otherwise (q holds the last
  * iterate), WFQ_ESINGULAR if some omega is 0.  Synchronises `stream`. */
