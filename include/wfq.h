@@ -259,7 +259,9 @@ int wfq_solve_gmres(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
  *   prec: precision of the block GMRES(50) that continues, from their iterate, the
  *         columns whose FP64 true residual is still above rel_tol at the end (basis cap
  *         reached, or rounding of the shared process): WFQ_PREC_MIXED or WFQ_PREC_FP64.
- * Needs a stored D (WFQ_STORE_F32X2, fastest, or WFQ_STORE_FP64), else WFQ_EUNSUPPORTED.
+ * D comes from the FP32 pair planes (WFQ_STORE_F32X2, fastest), the symmetric tiles
+ * (WFQ_STORE_F32X2_SYM), the FP64 D, or -- with none of them stored -- is regenerated from
+ * the coordinates in double-float for every product (near pairs in FP64; matrix-free).
  * stats: iters = Arnoldi steps the column used plus any continuation's; restarts = 1 +
  * the continuation's when a column was continued.  Other arguments and results as
  * wfq_solve_gmres. */

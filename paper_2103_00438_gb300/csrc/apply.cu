@@ -284,15 +284,13 @@ __device__ __forceinline__ void df_sqr_acc(float h, float l, float &sh, float &s
 // D_ik of Eq. 3 as a float pair.  Far pairs (r >= 6 sigma, where erf rounds to 1 in FP64):
 // 1/r from the float-pair coordinates -- r^2 in double-float, FP32 rsqrt refined by one
 // Newton step in double-float (relative error ~1e-13).  Near pairs and the diagonal: FP64.
-__device__ __forceinline__ void d_pair_df(const float4 *__restrict__ adf, const atom64_t *__restrict__ a64,
-                                          const double *__restrict__ eta, int64_t i, int64_t k, float &dh,
-                                          float &dl) {
+__device__ __forceinline__ void d_pair_df_v(float4 pi0, float4 pi1, float4 pk0, float4 pk1,
+                                            const atom64_t *__restrict__ a64, const double *__restrict__ eta,
+                                            int64_t i, int64_t k, float &dh, float &dl) {
     if (i == k) {
         df_split(eta[i], dh, dl);
         return;
     }
-    const float4 pi0 = adf[2 * i], pi1 = adf[2 * i + 1];   // (xh, xl, yh, yl), (zh, zl, w, -)
-    const float4 pk0 = adf[2 * k], pk1 = adf[2 * k + 1];
     float xh, xl, yh, yl, zh, zl;
     df_sub(pi0.x, pi0.y, pk0.x, pk0.y, xh, xl);
     df_sub(pi0.z, pi0.w, pk0.z, pk0.w, yh, yl);
@@ -314,6 +312,84 @@ __device__ __forceinline__ void d_pair_df(const float4 *__restrict__ adf, const 
     const float delta = __fsub_rn(1.0f, uh) - ul;   // 1 - r^2 y0^2, ~1e-7
     dh = y0;
     dl = 0.5f * y0 * delta;
+}
+
+__device__ __forceinline__ void d_pair_df(const float4 *__restrict__ adf, const atom64_t *__restrict__ a64,
+                                          const double *__restrict__ eta, int64_t i, int64_t k, float &dh,
+                                          float &dl) {
+    // (xh, xl, yh, yl), (zh, zl, w, -) float pairs per atom
+    d_pair_df_v(adf[2 * i], adf[2 * i + 1], adf[2 * k], adf[2 * k + 1], a64, eta, i, k, dh, dl);
+}
+
+// U[d][i] = sum_j D_ij x[d][j] for C <= 4 real vectors (direction-major, float-pair split
+// xh / xl), with D generated as float pairs from the coordinates (d_pair_df) -- the
+// matrix-free form of the shifted solver's product.  A warp owns MFV_ROWS rows; its lanes
+// walk the columns, each column's atom record and x loaded once for all the warp's rows.
+constexpr int MFV_ROWS = 2;
+template <int C>
+__global__ void __launch_bounds__(256) k_dotf_dfv(int64_t n, const float4 *__restrict__ adf,
+                                                  const atom64_t *__restrict__ a64, const double *__restrict__ eta,
+                                                  const float *__restrict__ xh, const float *__restrict__ xl,
+                                                  double *__restrict__ U) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = ((int64_t)blockIdx.x * 8 + warp) * MFV_ROWS;
+    float4 pi0[MFV_ROWS], pi1[MFV_ROWS];
+    float sh[MFV_ROWS][C], sl[MFV_ROWS][C];
+#pragma unroll
+    for (int r = 0; r < MFV_ROWS; ++r) {
+        const int64_t i = row0 + r < n ? row0 + r : n - 1;   // rows past n compute, never store
+        pi0[r] = adf[2 * i];
+        pi1[r] = adf[2 * i + 1];
+#pragma unroll
+        for (int d = 0; d < C; ++d) sh[r][d] = sl[r][d] = 0.f;
+    }
+    for (int64_t k = lane; k < n; k += 32) {
+        const float4 pk0 = adf[2 * k], pk1 = adf[2 * k + 1];
+        float xkh[C], xkl[C];
+#pragma unroll
+        for (int d = 0; d < C; ++d) {
+            xkh[d] = xh[(int64_t)d * n + k];
+            xkl[d] = xl[(int64_t)d * n + k];
+        }
+#pragma unroll
+        for (int r = 0; r < MFV_ROWS; ++r) {
+            const int64_t i = row0 + r < n ? row0 + r : n - 1;
+            float dh, dl;
+            d_pair_df_v(pi0[r], pi1[r], pk0, pk1, a64, eta, i, k, dh, dl);
+#pragma unroll
+            for (int d = 0; d < C; ++d) df_mac(dh, dl, xkh[d], xkl[d], sh[r][d], sl[r][d]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < MFV_ROWS; ++r)
+#pragma unroll
+        for (int d = 0; d < C; ++d)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh[r][d], off);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl[r][d], off);
+                df_add(sh[r][d], sl[r][d], oh, ol);
+            }
+    if (lane == 0)
+#pragma unroll
+        for (int r = 0; r < MFV_ROWS; ++r)
+            if (row0 + r < n)
+#pragma unroll
+                for (int d = 0; d < C; ++d) U[(int64_t)d * n + row0 + r] = (double)sh[r][d] + (double)sl[r][d];
+}
+
+int d_gemv_df_mf(const wfq_geom *g, int C, const float *xh, const float *xl, double *U, cudaStream_t s) {
+    const int64_t n = g->n;
+    const unsigned blocks = (unsigned)((n + 8 * MFV_ROWS - 1) / (8 * MFV_ROWS));
+    switch (C) {
+        case 1: k_dotf_dfv<1><<<blocks, 256, 0, s>>>(n, g->atomdf, g->atom64, g->eta, xh, xl, U); break;
+        case 2: k_dotf_dfv<2><<<blocks, 256, 0, s>>>(n, g->atomdf, g->atom64, g->eta, xh, xl, U); break;
+        case 3: k_dotf_dfv<3><<<blocks, 256, 0, s>>>(n, g->atomdf, g->atom64, g->eta, xh, xl, U); break;
+        default: k_dotf_dfv<4><<<blocks, 256, 0, s>>>(n, g->atomdf, g->atom64, g->eta, xh, xl, U); break;
+    }
+    note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
 }
 
 // As k_dgemm_df with the D tile generated per use (matrix-free); TN columns per thread.

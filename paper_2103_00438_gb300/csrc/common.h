@@ -253,6 +253,10 @@ struct SolveArgs {
     bool warm = false;
 };
 
+// U[d][i] = (D x_d)_i for C <= 4 real direction-major vectors given as float pairs, D
+// generated from the coordinates in double-float (matrix-free shifted product).
+int d_gemv_df_mf(const wfq_geom *g, int C, const float *xh, const float *xl, double *U, cudaStream_t s);
+
 int solve_gmres(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
 int solve_qmr(wfq_geom *g, const SolveArgs &a, cudaStream_t s);
 // Shifted GMRES (one real Arnoldi per direction for all frequencies); a.m caps the basis.

@@ -717,6 +717,13 @@ struct Arnoldi {
 
     // u = D v; xh / xl already hold v's float-pair split (written when v was normalised)
     int dmul(double *u) {
+        if (!g->Dsym && !g->Dfh && !g->D64) {   // matrix-free: D regenerated per product
+            KScope ks(g->ctx, WFQ_KT_DGEMV_DF, s, 0.0);
+            for (int d0 = 0; d0 < C; d0 += 4)
+                WFQ_TRY(d_gemv_df_mf(g, std::min(4, C - d0), xh.ptr + (int64_t)d0 * n, xl.ptr + (int64_t)d0 * n,
+                                     u + (int64_t)d0 * n, s));
+            return WFQ_OK;
+        }
         if (g->Dsym && !g->Dfh) {   // symmetric tiles: half the bytes, each tile used twice (the
                                     // full planes, when also stored, measured slightly faster)
             const int64_t T = g->sym_nt;
@@ -803,9 +810,6 @@ size_t shifted_footprint(const wfq_geom *g, int64_t ncols, int ndir, int m) {
 }
 
 int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
-    if (!g->Dsym && !g->Dfh && !g->D64)
-        return fail(WFQ_EUNSUPPORTED,
-                    "shifted GMRES needs a stored D (WFQ_STORE_F32X2_SYM, WFQ_STORE_F32X2 or WFQ_STORE_FP64)");
     wfq_ctx *ctx = g->ctx;
     const int64_t n = g->n, C = a.ndir, nc = a.col_omega ? a.ncols : a.nfreq * C;
     int m = a.m > 0 ? a.m : 600;

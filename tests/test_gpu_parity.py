@@ -468,11 +468,25 @@ def test_shifted_gmres_symmetric_tiles_equal_full_planes(W, ctx, S):
     assert max(s["rel_residual"] for s in sb) <= 1e-10
 
 
-def test_shifted_gmres_needs_stored_d(W, ctx, S):
-    g = W.Geometry(ctx, S.honeycomb_flake(3), _carbon(S), store=W.STORE_BF16X2)
-    with pytest.raises(W.WfqError) as e:
-        g.solve_gmres_shifted(S.ev([0.5]), [[1.0, 0, 0]])
-    assert e.value.code == -8
+def test_shifted_gmres_matrix_free_matches_lu(W, ctx, orc, S):
+    """No D stored: the shifted solver regenerates D from the coordinates in double-float
+    for every product (near pairs in FP64); every column equals its LU solve."""
+    xyz = S.nanotube(5, 5, 30)          # 600 atoms
+    p = S.carbon_params(1.04)
+    g = W.Geometry(ctx, xyz, p, store=0)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.2, 1.3])
+    dirs = np.eye(3)[:2]
+    q, st, status = g.solve_gmres_shifted(om, dirs, rel_tol=1e-10, max_iter=2000, prec=W.PREC_FP64)
+    assert status == "WFQ_OK"
+    al = g.polarizability(q)
+    for f in range(2):
+        for d in range(2):
+            c = f * 2 + d
+            q_lu, _ = sysm.solve(om[f], dirs[d], method="lu")
+            a_ref = orc.alpha(xyz, q_lu)
+            assert np.abs(al[c] - a_ref).max() <= 1e-8 * np.abs(a_ref).max(), (f, d)
+            assert st[c]["rel_residual"] <= 1e-10 and st[c]["restarts"] == 0
 
 
 # ----------------------------------------------------------------------------- edge cases
