@@ -1,8 +1,9 @@
-"""Seeded synthetic inputs: atomic structures, parameter sets, frequency grids.
+"""Seeded synthetic inputs: atomic structures, surface meshes, parameter sets, frequency grids.
 
-This module holds no arithmetic of the omega-FQ method itself -- only positions
-(bohr), parameter values (atomic units) and frequency lists.  It is the one
-module that both the CUDA path and the CPU oracle take their inputs from.
+This module holds no arithmetic of the omega-FQ method or of the BEM operator --
+only positions (bohr), surface geometry (normals, element areas, curvatures),
+parameter values (atomic units) and frequency lists.  It is the one module that
+both the CUDA path and the CPU oracle take their inputs from.
 
 Structures follow the systems of the paper's Section 4: chiral and armchair
 carbon nanotubes (Table "CNT data"), graphene disks cut from the honeycomb
@@ -230,6 +231,44 @@ def random_cluster(n: int, seed: int, spacing_bohr: float = 2.7, jitter: float =
     return xyz
 
 
+# --------------------------------------------------------------------------- surfaces
+# Collocation meshes for the continuum (BEM) operator of Section 2.3: one point per surface
+# element, with its outward unit normal, its area and the surface's mean curvature there.
+
+def spheroid_surface(n: int, a_bohr: float, b_bohr: float) -> dict:
+    """Spheroid x^2/b^2 + y^2/b^2 + z^2/a^2 = 1 (a = b: sphere) with n collocation points.
+
+    The points are a Fibonacci lattice on the unit sphere (polar cosine 1 - (2k+1)/n,
+    azimuth k times the golden angle; n cells of equal solid angle 4 pi / n) mapped to the
+    spheroid by (b sin t cos p, b sin t sin p, a cos t).  Each element's area is its solid
+    angle times the map's area factor b sqrt(a^2 sin^2 t + b^2 cos^2 t); the mean curvature
+    is the average of the meridian (a b / q^3) and parallel (a / (b q)) curvatures,
+    q = sqrt(a^2 sin^2 t + b^2 cos^2 t).  Seed-free.  Returns xyz, normal (n x 3), area,
+    curvature (n), bohr units."""
+    k = np.arange(n, dtype=np.float64)
+    ct = 1.0 - (2.0 * k + 1.0) / n
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    ph = math.pi * (3.0 - math.sqrt(5.0)) * k
+    a, b = float(a_bohr), float(b_bohr)
+    q = np.sqrt(a * a * st * st + b * b * ct * ct)
+    xyz = np.stack([b * st * np.cos(ph), b * st * np.sin(ph), a * ct], axis=1)
+    normal = np.stack([a * st * np.cos(ph), a * st * np.sin(ph), b * ct], axis=1) / q[:, None]
+    area = (4.0 * math.pi / n) * b * q
+    curvature = 0.5 * (a * b / q ** 3 + a / (b * q))
+    return {"xyz": np.ascontiguousarray(xyz), "normal": np.ascontiguousarray(normal),
+            "area": area, "curvature": curvature}
+
+
+def drude_metal_params(omega_p_ev: float = 5.9, gamma_ev: float = 0.1, eps_inf: float = 1.0,
+                       eps_out: float = 1.0) -> dict:
+    """Free-electron (Drude) metal in a uniform host: eps_in(w) = eps_inf - wp^2 / (w (w + i g)),
+    eps_out real.  Defaults: a sodium-like free-electron metal in vacuum (plasma energy 5.9 eV,
+    damping 0.1 eV; the sphere's dipole resonance eps_in = -2 eps_out lies at 3.41 eV).
+    Atomic units (hartree)."""
+    return {"eps_out": float(eps_out), "eps_inf": float(eps_inf),
+            "omega_p": omega_p_ev / HARTREE_EV, "gamma": gamma_ev / HARTREE_EV}
+
+
 def random_complex(shape, seed: int) -> np.ndarray:
     """Seeded standard complex normal array (apply-only inputs)."""
     rng = np.random.default_rng(seed)
@@ -249,6 +288,9 @@ def workload(name: str) -> dict:
               frequencies over 0.9-1.8 eV; x, y, z
     disk1m    graphene disk with ~1.01M sites, 1% vacancies; 16 frequencies over
               0.05-0.20 eV; direction x
+    bem_spheroid30k  continuum (BEM) prolate spheroid, semi-axes 20 nm (z) and 10 nm,
+              30000 collocation points, Drude metal in vacuum (drude_metal_params());
+              64 frequencies evenly over 2.0-4.5 eV; x, y, z
     """
     dirs3 = np.eye(3)
     if name == "flake1k":
@@ -266,6 +308,11 @@ def workload(name: str) -> dict:
         return {"xyz": graphene_disk(183.58, vacancy_frac=0.01, seed=20210304),
                 "params": carbon_params(1.84),
                 "omega": ev(np.linspace(0.05, 0.20, 16)), "dirs": dirs3[:1]}
+    if name == "bem_spheroid30k":
+        nm = 10.0 * BOHR_PER_ANGSTROM
+        surf = spheroid_surface(30000, 20.0 * nm, 10.0 * nm)
+        return {"xyz": surf["xyz"], "surface": surf, "bem": drude_metal_params(),
+                "omega": ev(np.linspace(2.0, 4.5, 64)), "dirs": dirs3}
     raise KeyError(name)
 
 
