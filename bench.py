@@ -226,6 +226,45 @@ def oracle_sample(wl, budget_s, cols):
     return solved, t_total, alphas, os.cpu_count()
 
 
+def is_bem(wl):
+    return "surface" in wl
+
+
+def make_geometry(wfq, ctx, wl, store, xyz=None):
+    """The workload's geometry: an omega-FQ structure, or a BEM surface (whose FP64 operator
+    is always stored)."""
+    if is_bem(wl):
+        s = wl["surface"]
+        return wfq.BemGeometry(ctx, s["xyz"] if xyz is None else xyz, s["normal"], s["area"], s["curvature"],
+                               wl["bem"], store=store | wfq.STORE_FP64)
+    return wfq.Geometry(ctx, wl["xyz"] if xyz is None else xyz, wl["params"], store=store)
+
+
+def oracle_sample_bem(wl, budget_s, cols, A=None):
+    """BEM workloads: solve sampled columns with the oracle's FP64 GMRES(50) on its dense
+    operator (oracle/bem.py; assembly not timed) to rel. residual 1e-10.
+    Returns (solves, seconds, {col: alpha}, cores, A)."""
+    from oracle import bem as ob
+    from oracle import oracle as orc
+    s = wl["surface"]
+    ndir = len(wl["dirs"])
+    if A is None:
+        A = ob.a_matrix(s["xyz"], s["normal"], s["area"], s["curvature"])
+    op = orc.Operator.dense(A)
+    alphas, t_total, solved = {}, 0.0, 0
+    for c in cols:
+        f, d = divmod(int(c), ndir)
+        R = ob.rhs(s["normal"], s["area"], wl["dirs"][d]).astype(complex)
+        t0 = time.perf_counter()
+        q, info = op.gmres(ob.z_of_omega(wl["omega"][f], wl["bem"]), R, restart=50, rel_tol=1e-10, max_iter=20000)
+        t_total += time.perf_counter() - t0
+        alphas[int(c)] = ob.alpha(s["xyz"], q)
+        solved += 1
+        if t_total >= budget_s:
+            break
+    return solved, t_total, alphas, os.cpu_count(), A
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -238,8 +277,12 @@ def run_reference(args, rank, world):
     order = rng.permutation(ncols)
     per_step = []
     k = 0
+    A = None
     for i in range(args.warmup + args.steps):
-        solved, secs, _, cores = oracle_sample(wl, args.cpu_budget_s, [order[k % ncols]])
+        if is_bem(wl):
+            solved, secs, _, cores, A = oracle_sample_bem(wl, args.cpu_budget_s, [order[k % ncols]], A)
+        else:
+            solved, secs, _, cores = oracle_sample(wl, args.cpu_budget_s, [order[k % ncols]])
         k += 1
         if i >= args.warmup:
             per_step.append(secs / max(solved, 1))
@@ -251,8 +294,8 @@ def run_reference(args, rank, world):
            "data": "synthetic", "config": {"workload": args.workload, "n_atoms": len(wl["xyz"]),
                                              "columns": ncols},
            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": "one (omega, direction) column per step, FP64 GMRES(50) on stored D "
-                                      "to rel. residual 1e-10"},
+                            "sample": "one (omega, direction) column per step, FP64 GMRES(50) on the stored "
+                                      "%s to rel. residual 1e-10" % ("dense BEM operator" if is_bem(wl) else "D")},
            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -267,6 +310,8 @@ def run_ours(args, rank, world, dist):
         return run_serve(args, rank, world, dist)
     if args.mode == "spectrum":
         return run_spectrum(args, rank, world, dist)
+    if args.workload.startswith("bem_"):
+        return run_bem(args, rank, world, dist)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     wl = workload(args.workload)
@@ -492,6 +537,126 @@ def run_ours(args, rank, world, dist):
                                "sample": f"{solved} sampled (omega, direction) columns of the same workload, "
                                          "FP64 GMRES(50) on stored FP64 D to rel. residual 1e-10 "
                                          "(D assembly not timed)"}
+        out["accuracy"]["alpha_rel_err_vs_oracle_sampled"] = max(errs) if errs else None
+        out["accuracy"]["alpha_columns_checked"] = sorted(alphas)
+    g.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_bem(args, rank, world, dist):
+    """The continuum BEM operator of Section 2.3 (Eq. 21-22) through the same shifted
+    solver: every (omega, direction) column of the workload in one shifted GMRES solve,
+    the operator streamed from its FP32 pair planes (the FP64 copy serves the residuals)."""
+    import torch
+    from paper_2103_00438_gb300 import wfq
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    wl = workload(args.workload)
+    xyz, om, dirs = wl["xyz"], wl["omega"], wl["dirs"]
+    n, nf, nd = len(xyz), len(om), len(dirs)
+    ncols = nf * nd
+    ctx = wfq.Context(local)
+    store = wfq.STORE_FP64 | wfq.STORE_F32X2
+    g = make_geometry(wfq, ctx, wl, store)
+    stream = torch.cuda.current_stream()
+    q = torch.empty((n, ncols), dtype=torch.complex128, device="cuda")
+
+    def step():
+        _, st, status = g.solve_gmres_shifted(om, dirs, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_FP64, out=q,
+                                              stream=stream)
+        return st, status, g.polarizability(q, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile(True)
+    launches0 = wfq.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    res = []
+    for _ in range(args.steps):
+        res.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = wfq.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist)
+    gv_n, gv_ms, gv_bytes = ctx.profile_read(wfq.KT_DGEMV_DF)
+    sp_n, sp_ms, _ = ctx.profile_read(wfq.KT_SPARSE)
+    or_n, or_ms, _ = ctx.profile_read(wfq.KT_ORTHO)
+    ctx.profile(False)
+    st, status, alpha = res[-1]
+    good = sum(1 for x in st if x["rel_residual"] <= 1e-8)
+    iters = [x["iters"] for x in st]
+    peaks, peak_src = load_peaks()
+    roof = None
+    if gv_n:
+        achieved = gv_bytes / (gv_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": DGEMV_DRAM_BYTES_PER_ENTRY * n * (-(-n // 4) * 4),
+                "traffic_source": "ncu dram__bytes_read+write of k_dgemv_df at N = 8200 (same kernel, same "
+                                  "plane layout), scaled per stored entry to this N",
+                "kernel": "k_dgemv_df (double-float product of the BEM operator's FP32 pair planes)",
+                "launches": gv_n, "avg_ms": gv_ms / gv_n, "bytes_per_launch": gv_bytes / gv_n,
+                "peak_source": peak_src + " hbm_gbs (STREAM-style copy)"}
+    out = {"metric": "freq-point solves/s", "value": good * args.steps * world / (ms / 1e3), "unit": "solves/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32x2(double-float)+f64", "data": "synthetic",
+           "config": {"workload": args.workload, "operator": "continuum BEM (Eq. 21-22), charge form, collocation",
+                      "n_elements": n, "nfreq": nf, "ndir": nd, "columns": ncols, "rel_tol": 1e-8,
+                      "solver": "shifted gmres (one real Arnoldi per direction, all frequencies)",
+                      "parallelism": f"replicas{world}",
+                      "l2": "inputs larger than L2 (FP32 pair planes of the operator, %.2f GB)" % (8.0 * n * n / 1e9)},
+           "accuracy": {"max_rel_residual": max(x["rel_residual"] for r in res for x in r[0]),
+                        "columns_converged": good, "iters_min_mean_max": [min(iters), float(np.mean(iters)),
+                                                                          max(iters)], "status": status},
+           "kernel_ms_per_step": {"dgemv_df": gv_ms / args.steps, "shift_copy": sp_ms / args.steps,
+                                  "ortho_phase": or_ms / args.steps},
+           "roofline": roof, "clocks": clk, "gpu_launches": int(launches)}
+    if not args.no_e2e:
+        s = wl["surface"]
+        pins = {k: torch.from_numpy(np.ascontiguousarray(s[k])).pin_memory().numpy()
+                for k in ("xyz", "normal", "area", "curvature")}
+        q_host = torch.empty((n, ncols), dtype=torch.complex128).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ge = wfq.BemGeometry(ctx, pins["xyz"], pins["normal"], pins["area"], pins["curvature"], wl["bem"],
+                                 store=store)
+            ge.solve_gmres_shifted(om, dirs, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_FP64, out=q_host.numpy())
+            ge.polarizability(q_host.numpy())
+            ge.close()
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - t0, dist)
+        out["e2e"] = {"value": good * args.steps * world / te, "unit": "solves/s",
+                      "h2d_bytes_per_step": int(sum(v.nbytes for v in pins.values()) + om.nbytes + dirs.nbytes),
+                      "d2h_bytes_per_step": int(n * ncols * 16 + ncols * 3 * 16),
+                      "includes": "operator build (FP64 and FP32 pair planes) from host surface arrays, solve, "
+                                  "alpha"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        from oracle import build as obuild
+        obuild.build()
+        rng = np.random.default_rng(20210302)
+        cols = rng.permutation(ncols)[:4]
+        solved, secs, alphas, cores, _ = oracle_sample_bem(wl, args.cpu_budget_s, cols)
+        errs = [float(np.abs(alpha[c] - a).max() / np.abs(a).max()) for c, a in alphas.items()]
+        out["cpu_baseline"] = {"value": solved / secs, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{solved} sampled (omega, direction) columns of the same workload, "
+                                         "FP64 GMRES(50) on the oracle's dense BEM operator to rel. residual "
+                                         "1e-10 (assembly not timed)"}
         out["accuracy"]["alpha_rel_err_vs_oracle_sampled"] = max(errs) if errs else None
         out["accuracy"]["alpha_columns_checked"] = sorted(alphas)
     g.close()
@@ -809,25 +974,27 @@ def run_spectrum(args, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     wl = workload(args.workload)
-    xyz, p, dirs = wl["xyz"], wl["params"], np.eye(3)
+    xyz, dirs = wl["xyz"], np.eye(3)
     lo, hi = float(wl["omega"][0]), float(wl["omega"][-1])
     ev_lo, ev_hi = lo * S.HARTREE_EV, hi * S.HARTREE_EV
     grid_ev = np.round(np.arange(ev_lo, ev_hi + 1e-9, 0.01), 6)
     om = S.ev(grid_ev)
     n, nf = len(xyz), len(om)
     ctx = wfq.Context(local)
-    g = wfq.Geometry(ctx, xyz, p, store=wfq.STORE_F32X2)
+    g = make_geometry(wfq, ctx, wl, wfq.STORE_F32X2)
+    # precision of any continuation: FP64 for a BEM surface (no bf16 planes stored)
+    prec = wfq.PREC_FP64 if is_bem(wl) else wfq.PREC_MIXED
     stream = torch.cuda.current_stream()
     q = torch.empty((n, nf * 3), dtype=torch.complex128, device="cuda")
     for _ in range(max(args.warmup, 1)):
-        g.solve_gmres_shifted(om, dirs, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED, out=q, stream=stream)
+        g.solve_gmres_shifted(om, dirs, rel_tol=1e-8, max_iter=4000, prec=prec, out=q, stream=stream)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        _, st, status = g.solve_gmres_shifted(om, dirs, rel_tol=1e-8, max_iter=4000, prec=wfq.PREC_MIXED, out=q,
+        _, st, status = g.solve_gmres_shifted(om, dirs, rel_tol=1e-8, max_iter=4000, prec=prec, out=q,
                                               stream=stream)
     alpha = g.polarizability(q, stream=stream)
     e1.record(stream)

@@ -74,6 +74,16 @@ typedef struct {
     double cutoff_eps; /* Kbar keeps pair (i,j) iff 1 - f(r_ij) >= cutoff_eps; 0 keeps all */
 } wfq_params;
 
+/* The continuum (BEM) operator of Section 2.3 (Eq. 21, Eq. 22): a particle with the
+ * Drude permittivity eps_in(w) = eps_inf - omega_p^2 / (w (w + i gamma)) in a host of
+ * real permittivity eps_out.  Atomic units (hartree). */
+typedef struct {
+    double eps_out;    /* host permittivity, real, > 0 */
+    double eps_inf;    /* background permittivity of the particle, real, > 0 */
+    double omega_p;    /* plasma frequency, > 0 */
+    double gamma;      /* damping rate, >= 0 */
+} wfq_bem_params;
+
 /* Storage of D chosen at geometry build (bit flags).  With no flag set D is never
  * stored: every apply recomputes its entries from the coordinates (matrix-free). */
 #define WFQ_STORE_FP64   1u  /* D in FP64, N*N*8 bytes: FP64 applies and residuals */
@@ -173,6 +183,39 @@ int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms
  * closer than 1e-8 bohr.  *out is set on success. */
 int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double *eta,
                        const wfq_params *p, uint32_t store, wfq_geom **out);
+
+/* Builds a geometry for the continuum BEM operator of Section 2.3 (the comparison with
+ * continuum approaches), which has the same algebraic form as the omega-FQ system: a real
+ * frequency-independent matrix with a uniform complex shift.  Eq. 21,
+ * (Lambda(w) I + F) sigma = -dphi/dn with Lambda(w) = 2 pi (eps_out + eps_in(w)) /
+ * (eps_out - eps_in(w)) and F_ij = n_i . (r_i - r_j) / |r_i - r_j|^3 (Eq. 22), is
+ * discretised by collocation at n surface elements and solved as (A - zI) q = R for the
+ * element charges q_i = a_i sigma_i:
+ *     A_ij = a_i n_i . (r_i - r_j) / |r_i - r_j|^3  (i != j),
+ *     A_ii = H_i sqrt(pi a_i)  (Eq. 22's principal value over the element itself, taken
+ *            as a flat disk of area a_i on a surface of mean curvature H_i),
+ *     z(w) = -Lambda(w),   R_i = -E0 a_i (n_i . k)  (the field phi = -E0 k . r; the sign
+ *            is the one for which q is the physical charge: the printed right-hand side
+ *            -dphi/dn gives -q).
+ * The polarizability (wfq_polarizability) is then sum_i q_i r_i / E0 as for omega-FQ.
+ * xyz: host n x 3 collocation points (bohr); normal: host n x 3 outward unit normals
+ * (norm within 1e-6 of 1); area: host n element areas (> 0); curvature: host n mean
+ * curvatures H_i (1 / bohr, positive where the surface bends away from its outward normal,
+ * as on a sphere), or NULL for flat elements (H = 0).  store: must include WFQ_STORE_FP64;
+ * WFQ_STORE_F32X2 (the shifted solver's fastest operator) and WFQ_STORE_BF16X2 (needed by
+ * WFQ_PREC_MIXED) are optional; WFQ_STORE_F32X2_SYM is rejected (A is not symmetric).
+ * Operator entries are never regenerated from the coordinates (no matrix-free path).
+ * Every entry point that takes a geometry accepts a BEM geometry, with these differences:
+ * wfq_apply computes y = A x - z x; wfq_rhs returns the R above; wfq_solve_qmr returns
+ * WFQ_EUNSUPPORTED (its J-symmetry needs A = (Kbar - P) D with D symmetric);
+ * WFQ_PREC_MIXED without WFQ_STORE_BF16X2 and wfq_apply_mixed_noalloc return
+ * WFQ_EUNSUPPORTED; a frequency at which eps_in = eps_out (Lambda infinite) is WFQ_EINVAL,
+ * omega = 0 WFQ_ESINGULAR.  Fails with WFQ_EINVAL for n < 1, non-finite input, a
+ * non-positive area or parameter, a normal that is not a unit vector, or two elements
+ * closer than 1e-8 bohr.  *out is set on success. */
+int wfq_build_bem_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double *normal,
+                           const double *area, const double *curvature, const wfq_bem_params *p,
+                           uint32_t store, wfq_geom **out);
 
 int wfq_free_geometry(wfq_geom *g);
 
@@ -301,7 +344,9 @@ int wfq_polarizability(wfq_geom *g, int64_t ncols, const double *q, double E0,
  * wfq_solve_gmres_shifted: one real Arnoldi process per distinct field direction of the
  * batch for all its frequencies; m is not used, continuations run GMRES(50)); otherwise
  * by mixed-precision GMRES(m) with FP64 refinement (as wfq_solve_gmres with
- * WFQ_PREC_MIXED).
+ * WFQ_PREC_MIXED).  BEM geometries (wfq_build_bem_geometry, which always store the FP64
+ * operator) take the shifted path; their continuations run in FP64 unless the bf16 planes
+ * are stored too.
  *   budget_bytes: device memory the batches in flight may use together (Krylov bases,
  *   blocks, scratch; the geometries themselves are not counted).  A batch that alone
  *   exceeds it still runs when nothing else is in flight. */

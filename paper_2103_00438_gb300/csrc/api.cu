@@ -143,7 +143,7 @@ static int galloc(wfq_geom *g, T **p, size_t count) {
 static void free_geom(wfq_geom *g) {
     void *ptrs[] = {g->xyz, g->atom64, g->atom32, g->atomdf, g->eta, g->rowptr, g->col,
                     g->val64, g->val32, g->D64, g->Dhi, g->Dlo, g->Dfh, g->Dfl,
-                    g->Dsym, g->sym_items, g->sym_item_start};
+                    g->Dsym, g->sym_items, g->sym_item_start, g->elem};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -415,6 +415,86 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     return WFQ_OK;
 }
 
+int wfq_build_bem_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double *normal, const double *area,
+                           const double *curvature, const wfq_bem_params *p, uint32_t store, wfq_geom **out) {
+    if (!ctx || !out) return fail(WFQ_EINVAL, "NULL context or out-pointer");
+    *out = nullptr;
+    if (n < 1) return fail(WFQ_EINVAL, "n must be >= 1");
+    if (n > INT32_MAX) return fail(WFQ_EINVAL, "n exceeds 2^31 - 1");
+    if (!xyz || !normal || !area || !p) return fail(WFQ_EINVAL, "xyz, normal, area or params is NULL");
+    if (store & ~(WFQ_STORE_FP64 | WFQ_STORE_BF16X2 | WFQ_STORE_F32X2 | WFQ_STORE_F32X2_SYM))
+        return fail(WFQ_EINVAL, "unknown storage flag");
+    if (!(store & WFQ_STORE_FP64)) return fail(WFQ_EINVAL, "the BEM operator needs WFQ_STORE_FP64");
+    if (store & WFQ_STORE_F32X2_SYM) return fail(WFQ_EINVAL, "the BEM operator is not symmetric: no WFQ_STORE_F32X2_SYM");
+    if (!(std::isfinite(p->eps_out) && p->eps_out > 0.0 && std::isfinite(p->eps_inf) && p->eps_inf > 0.0 &&
+          std::isfinite(p->omega_p) && p->omega_p > 0.0 && std::isfinite(p->gamma) && p->gamma >= 0.0))
+        return fail(WFQ_EINVAL, "BEM parameters: eps_out, eps_inf, omega_p must be finite and > 0, gamma finite and >= 0");
+    if (!finite_all(xyz, 3 * n) || !finite_all(normal, 3 * n) || !finite_all(area, n) ||
+        (curvature && !finite_all(curvature, n)))
+        return fail(WFQ_EINVAL, "non-finite position, normal, area or curvature");
+    std::vector<elem64_t> el(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double nx = normal[3 * i], ny = normal[3 * i + 1], nz = normal[3 * i + 2];
+        if (std::fabs(std::sqrt(nx * nx + ny * ny + nz * nz) - 1.0) > 1e-6)
+            return fail(WFQ_EINVAL, "normal " + std::to_string(i) + " is not a unit vector");
+        if (!(area[i] > 0.0)) return fail(WFQ_EINVAL, "element areas must be > 0");
+        const double H = curvature ? curvature[i] : 0.0;
+        // self coefficient: Eq. 22's principal value over the element itself, a disk of the
+        // element's area (radius rho = sqrt(a / pi)) on a surface of mean curvature H, where
+        // n . (r_i - r') / |r_i - r'|^3 is about H / (2 s) at distance s: pi H rho in total.
+        // The charge form (row scaled by a_i, unknown a_i sigma_i) leaves it unchanged.
+        el[i] = elem64_t{xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], nx, ny, nz, area[i],
+                         H * std::sqrt(M_PI * area[i])};
+    }
+    DeviceGuard dg(ctx->device);
+    auto *g = new wfq_geom;
+    g->ctx = ctx;
+    g->op = OP_BEM;
+    g->n = n;
+    g->npad = round_up(n, kTilePad);
+    g->ldf = round_up(n, 4);
+    g->bem = *p;
+    g->store = store;
+    g->nnz = 0;
+    int rc = WFQ_OK;
+    auto bail = [&](int code) {
+        free_geom(g);
+        return code;
+    };
+    if ((rc = galloc(g, &g->xyz, 3 * n))) return bail(rc);
+    if ((rc = galloc(g, &g->elem, n))) return bail(rc);
+    if ((rc = galloc(g, &g->rowptr, n + 1))) return bail(rc);   // empty sparse term
+    if ((rc = galloc(g, &g->D64, (size_t)n * n))) return bail(rc);
+    if (store & WFQ_STORE_BF16X2) {
+        if ((rc = galloc(g, &g->Dhi, (size_t)g->npad * g->npad))) return bail(rc);
+        if ((rc = galloc(g, &g->Dlo, (size_t)g->npad * g->npad))) return bail(rc);
+    }
+    if (store & WFQ_STORE_F32X2) {
+        if ((rc = galloc(g, &g->Dfh, (size_t)n * g->ldf))) return bail(rc);
+        if ((rc = galloc(g, &g->Dfl, (size_t)n * g->ldf))) return bail(rc);
+    }
+    int *close = nullptr;
+    if ((rc = galloc(g, &close, 1))) return bail(rc);
+    g->bytes -= sizeof(int);
+    auto done = [&](int code) {
+        cudaFree(close);
+        return code == WFQ_OK ? WFQ_OK : bail(code);
+    };
+    cudaError_t e = cudaMemcpy(g->xyz, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->elem, el.data(), sizeof(elem64_t) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(g->rowptr, 0, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMemset(close, 0, sizeof(int));
+    if (e != cudaSuccess) return done(fail(WFQ_ECUDA, std::string("upload: ") + cudaGetErrorString(e)));
+    if ((rc = launch_build_bem(g, close, nullptr))) return done(rc);
+    int close_h = 0;
+    e = cudaMemcpy(&close_h, close, sizeof(int), cudaMemcpyDeviceToHost);   // synchronises the build
+    if (e != cudaSuccess) return done(fail(WFQ_ECUDA, std::string("BEM build: ") + cudaGetErrorString(e)));
+    if (close_h) return done(fail(WFQ_EINVAL, "two surface elements closer than 1e-8 bohr"));
+    done(WFQ_OK);
+    *out = g;
+    return WFQ_OK;
+}
+
 int wfq_free_geometry(wfq_geom *g) {
     if (!g) return WFQ_OK;
     DeviceGuard dg(g->ctx->device);
@@ -441,7 +521,14 @@ int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, vo
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int64_t n = g->n, nc = n * ncplx;
     std::vector<double2> zh(ncplx);
-    for (int64_t c = 0; c < ncplx; ++c) zh[c] = z_of_omega(g->p, omega[c]);
+    if (g->op == OP_BEM && prec == WFQ_PREC_MIXED && !g->Dhi)
+        return fail(WFQ_EUNSUPPORTED, "the mixed apply of a BEM geometry needs WFQ_STORE_BF16X2");
+    const ShiftModel zm = shift_model(g);
+    for (int64_t c = 0; c < ncplx; ++c) {
+        zh[c] = z_eval(zm, omega[c]);
+        if (!(std::isfinite(zh[c].x) && std::isfinite(zh[c].y)))
+            return fail(WFQ_EINVAL, "z(omega) is not finite (BEM: omega = 0 or eps_in = eps_out)");
+    }
     DevBuf<double2> z;
     WFQ_TRY(z.alloc(g->ctx, ncplx, s));
     WFQ_CUDA(cudaMemcpyAsync(z.ptr, zh.data(), sizeof(double2) * ncplx, cudaMemcpyHostToDevice, s));
@@ -503,6 +590,19 @@ static int solve_common(Solver kind, wfq_geom *g, int64_t nfreq, const double *o
         return fail(WFQ_EINVAL, "non-finite omega / direction or E0 = 0");
     for (int64_t f = 0; f < nfreq; ++f)
         if (omega[f] == 0.0) return fail(WFQ_ESINGULAR, "omega = 0: z(0) = 0 and A is singular");
+    if (g->op == OP_BEM) {
+        if (kind == SOLVE_QMR)
+            return fail(WFQ_EUNSUPPORTED, "J-symmetric QMR needs A = (Kbar - P) D with D symmetric; "
+                                          "the BEM operator has no such factor");
+        if (prec == WFQ_PREC_MIXED && !g->Dhi)
+            return fail(WFQ_EUNSUPPORTED, "WFQ_PREC_MIXED on a BEM geometry needs WFQ_STORE_BF16X2");
+        const ShiftModel zm = shift_model(g);
+        for (int64_t f = 0; f < nfreq; ++f) {
+            const double2 z = z_eval(zm, omega[f]);
+            if (!(std::isfinite(z.x) && std::isfinite(z.y)))
+                return fail(WFQ_EINVAL, "eps_in(omega) = eps_out: Lambda(omega) is infinite");
+        }
+    }
     DeviceGuard dg(g->ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int64_t cc = nfreq * ndir;

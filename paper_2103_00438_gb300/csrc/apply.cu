@@ -378,7 +378,16 @@ __global__ void __launch_bounds__(256) k_dotf_dfv(int64_t n, const float4 *__res
                 for (int d = 0; d < C; ++d) U[(int64_t)d * n + row0 + r] = (double)sh[r][d] + (double)sl[r][d];
 }
 
+// A BEM geometry stores its operator; the kernels that regenerate D from the coordinates
+// (Eq. 3) must never see one.
+static int require_wfq(const wfq_geom *g) {
+    if (g->op != OP_WFQ)
+        return fail(WFQ_EUNSUPPORTED, "matrix-free products regenerate the omega-FQ D; a BEM geometry stores its operator");
+    return WFQ_OK;
+}
+
 int d_gemv_df_mf(const wfq_geom *g, int C, const float *xh, const float *xl, double *U, cudaStream_t s) {
+    WFQ_TRY(require_wfq(g));
     const int64_t n = g->n;
     const unsigned blocks = (unsigned)((n + 8 * MFV_ROWS - 1) / (8 * MFV_ROWS));
     switch (C) {
@@ -454,6 +463,7 @@ __global__ void __launch_bounds__(256) k_dotf_df(int64_t n, int64_t C, const flo
 int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
     if (!g->D64 && !g->Dfh) {
         // matrix-free double-float product
+        WFQ_TRY(require_wfq(g));
         const int64_t n = g->n, C = 2 * cc;
         if (C <= 2) return d_apply_fp64(g, cc, X, U, s);
         KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);
@@ -507,6 +517,7 @@ int d_apply_fp64(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cu
         if (g->D64) {
             k_dgemm<<<grid, 256, 0, s>>>(n, C, g->D64, x, u);
         } else {
+            WFQ_TRY(require_wfq(g));
             k_dotf<<<grid, 256, 0, s>>>(n, C, g->atom64, g->eta, x, u);
         }
         note_launch();
@@ -615,12 +626,35 @@ __global__ void __launch_bounds__(128) k_sparse_nbrs(int64_t n, const int64_t *_
     }
 }
 
+// BEM geometries (no sparse term): Y = U - z_c X elementwise, column c = e % cc.
+template <class V>
+__global__ void __launch_bounds__(256) k_shift_only(int64_t total, int64_t cc, const V *__restrict__ U,
+                                                    const V *__restrict__ X, const double2 *__restrict__ z,
+                                                    V *__restrict__ Y) {
+    using R = typename CplxT<V>::R;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const double2 zc = z[e % cc];
+    const R zr = (R)zc.x, zi = (R)zc.y;
+    const V u = U[e], xv = X[e];
+    V out;
+    out.x = u.x - (zr * xv.x - zi * xv.y);
+    out.y = u.y - (zr * xv.y + zi * xv.x);
+    Y[e] = out;
+}
+
 template <class V, class VAL>
 static int sparse_shift_impl(const wfq_geom *g, int64_t cc, const V *U, const V *X, const double2 *z,
                              V *Y, const VAL *val, cudaStream_t s) {
     const int64_t n = g->n;
     unsigned blocks = (unsigned)((n * 32 + 127) / 128);
     KScope ks(g->ctx, WFQ_KT_SPARSE, s);
+    if (g->op == OP_BEM) {
+        const int64_t total = n * cc;
+        k_shift_only<V><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(total, cc, U, X, z, Y); note_launch();
+        WFQ_CUDA(cudaGetLastError());
+        return WFQ_OK;
+    }
     switch (cc) {
         case 1: k_sparse_nbrs<V, VAL, 1><<<blocks, 128, 0, s>>>(n, g->rowptr, g->col, val, U, X, z, Y); note_launch(); break;
         case 2: k_sparse_nbrs<V, VAL, 2><<<blocks, 128, 0, s>>>(n, g->rowptr, g->col, val, U, X, z, Y); note_launch(); break;
@@ -684,6 +718,7 @@ size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc) {
 
 int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
                   cudaStream_t s) {
+    if (!g->Dhi) WFQ_TRY(require_wfq(g));
     const int64_t C = 2 * cc, cpad = mixed_cpad(cc), npad = g->npad;
     __nv_bfloat16 *xhi = reinterpret_cast<__nv_bfloat16 *>(scratch);
     __nv_bfloat16 *xlo = xhi + cpad * npad;

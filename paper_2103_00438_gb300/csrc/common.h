@@ -68,6 +68,43 @@ struct __align__(32) atom64_t {
     double x, y, z, w;
 };
 
+// Operator family of a geometry: the omega-FQ operator A = (Kbar - P) D (Eq. 14, 17), or
+// the continuum BEM operator of Eq. 21-22 in charge form (A = F scaled by the element
+// areas, no sparse term, z = -Lambda(w)).
+enum OpKind { OP_WFQ = 0, OP_BEM = 1 };
+
+// Per-element record of the BEM operator: collocation point, outward unit normal, area and
+// self coefficient (the principal value of Eq. 22 over the element itself).
+struct __align__(64) elem64_t {
+    double x, y, z, nx, ny, nz, area, self;
+};
+
+// The frequency-dependent shift z(w) of a geometry's operator family.
+struct ShiftModel {
+    int op;
+    double n0, tau;                       // omega-FQ, Eq. 12
+    double eps_out, eps_inf, wp, gamma;   // BEM: Drude particle in a uniform host
+};
+
+// omega-FQ: z = -(w / (2 n0 tau)) (w tau + i)  (Eq. 12).
+// BEM: z = -Lambda(w) = -2 pi (eps_out + eps_in) / (eps_out - eps_in)  (Eq. 21), with
+// eps_in = eps_inf - wp^2 / (w (w + i gamma)) = eps_inf - wp^2 / (w^2 + gamma^2)
+//          + i wp^2 gamma / (w (w^2 + gamma^2)).
+__host__ __device__ inline double2 z_eval(const ShiftModel &m, double w) {
+    if (m.op == OP_BEM) {
+        const double den = w * w + m.gamma * m.gamma;
+        const double er = m.eps_inf - m.wp * m.wp / den;
+        const double ei = m.wp * m.wp * m.gamma / (w * den);
+        const double ar = m.eps_out + er, ai = ei;     // eps_out + eps_in
+        const double br = m.eps_out - er, bi = -ei;    // eps_out - eps_in
+        const double bb = br * br + bi * bi;
+        const double two_pi = 6.283185307179586476925286766559;
+        return make_double2(-two_pi * (ar * br + ai * bi) / bb, -two_pi * (ai * br - ar * bi) / bb);
+    }
+    const double f = -w / (2.0 * m.n0 * m.tau);
+    return make_double2(f * w * m.tau, f);
+}
+
 }  // namespace wfq
 
 namespace wfq {
@@ -104,9 +141,11 @@ struct wfq_ctx {
 
 struct wfq_geom {
     wfq_ctx *ctx = nullptr;
-    int64_t n = 0;      // atoms
+    int op = wfq::OP_WFQ;   // operator family (wfq::OpKind)
+    int64_t n = 0;      // atoms (BEM: surface elements)
     int64_t npad = 0;   // n rounded up to kTilePad (bf16 plane dimension)
     wfq_params p{};
+    wfq_bem_params bem{};   // BEM geometries only
     uint32_t store = 0;
     int64_t nnz = 0;
     size_t bytes = 0;   // device bytes held
@@ -117,6 +156,7 @@ struct wfq_geom {
     float4 *atom32 = nullptr;   // (x, y, z, width), npad (padding: far away, width 1)
     float4 *atomdf = nullptr;   // 2 per atom: (xh, xl, yh, yl), (zh, zl, width, 0) float pairs
     double *eta = nullptr;      // n
+    wfq::elem64_t *elem = nullptr;   // BEM geometries: n element records
 
     // Kbar CSR (device)
     int64_t *rowptr = nullptr;  // n + 1
@@ -189,6 +229,9 @@ int build_kbar_csr(int64_t n, const double *xyz, const wfq_params &p, std::vecto
                    std::vector<int32_t> &col, std::vector<double> &val);
 
 int launch_build_d(const wfq_geom *g, cudaStream_t s);
+// BEM geometries: the operator's entries into the requested storages; *close is set
+// non-zero (device int) when two elements lie closer than 1e-8 bohr.
+int launch_build_bem(const wfq_geom *g, int *close, cudaStream_t s);
 int launch_rhs(const wfq_geom *g, int ndir, const double *dirs_dev, double E0, double *R,
                cudaStream_t s);
 int launch_polarizability(const wfq_geom *g, int64_t ncols, const double2 *q, double E0,
@@ -212,7 +255,7 @@ size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc);
 int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
                   cudaStream_t s);
 
-// Y = Kbar U - P U - z_c X   (z: device, cc values)
+// Y = Kbar U - P U - z_c X   (z: device, cc values); BEM geometries: Y = U - z_c X
 int sparse_shift_fp64(const wfq_geom *g, int64_t cc, const double2 *U, const double2 *X,
                       const double2 *z, double2 *Y, cudaStream_t s);
 int sparse_shift_fp32(const wfq_geom *g, int64_t cc, const float2 *U, const float2 *X,
@@ -273,10 +316,17 @@ int finish_columns(wfq_geom *g, const SolveArgs &a, const std::vector<int> &iter
 // Device bytes a block solve of `cc` columns allocates (Krylov basis, FP64 blocks, scratch).
 size_t solve_footprint(const wfq_geom *g, int64_t cc, int m, int prec);
 
-// z(omega) of Eq. 12 for the geometry's parameters.
-inline double2 z_of_omega(const wfq_params &p, double omega) {
-    double f = -omega / (2.0 * p.n0 * p.tau);
-    return make_double2(f * omega * p.tau, f);
+// The shift model of a geometry's operator family (z_eval).
+inline ShiftModel shift_model(const wfq_geom *g) {
+    ShiftModel m{};
+    m.op = g->op;
+    m.n0 = g->p.n0;
+    m.tau = g->p.tau;
+    m.eps_out = g->bem.eps_out;
+    m.eps_inf = g->bem.eps_inf;
+    m.wp = g->bem.omega_p;
+    m.gamma = g->bem.gamma;
+    return m;
 }
 
 }  // namespace wfq

@@ -154,6 +154,58 @@ __global__ void k_build_d(const atom64_t *__restrict__ atom, const double *__res
     }
 }
 
+// BEM operator (Eq. 22 in charge form), one thread per (i, j) with j fastest, into the same
+// storages as D (FP64, bf16 hi/lo planes zero-padded to npad, FP32 hi/lo planes of ldf
+// columns): A_ij = a_i n_i . (r_i - r_j) / |r_i - r_j|^3, A_ii = the element's self
+// coefficient.  *close is set when two distinct elements lie closer than 1e-8 bohr.
+__global__ void k_build_bem(const elem64_t *__restrict__ el, int64_t n, int64_t npad, int64_t lim,
+                            double *__restrict__ D64, __nv_bfloat16 *__restrict__ hi,
+                            __nv_bfloat16 *__restrict__ lo, int64_t ldf, float *__restrict__ fh,
+                            float *__restrict__ fl, int *__restrict__ close) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= lim || j >= lim) return;
+    double v = 0.0;
+    if (i < n && j < n) {
+        const elem64_t a = el[i];
+        if (i == j) {
+            v = a.self;
+        } else {
+            const elem64_t b = el[j];
+            const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < 1e-16) {
+                atomicOr(close, 1);
+            } else {
+                v = a.area * (a.nx * dx + a.ny * dy + a.nz * dz) / (r2 * sqrt(r2));
+            }
+        }
+    }
+    if (D64 && i < n && j < n) D64[i * n + j] = v;
+    if (fh && i < n && j < ldf) {
+        const float h = (float)v;
+        fh[i * ldf + j] = h;
+        fl[i * ldf + j] = (float)(v - (double)h);
+    }
+    if (hi) {
+        __nv_bfloat16 h = __double2bfloat16(v);
+        __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
+        hi[i * npad + j] = h;
+        lo[i * npad + j] = l;
+    }
+}
+
+int launch_build_bem(const wfq_geom *g, int *close, cudaStream_t s) {
+    const int64_t lim = g->Dhi ? g->npad : (g->Dfh ? g->ldf : g->n);   // ldf <= npad
+    dim3 block(64, 4);
+    dim3 grid((unsigned)((lim + 63) / 64), (unsigned)((lim + 3) / 4));
+    if (grid.y > 65535u) return fail(WFQ_EUNSUPPORTED, "stored BEM operator with more than 262140 rows");
+    k_build_bem<<<grid, block, 0, s>>>(g->elem, g->n, g->npad, lim, g->D64, g->Dhi, g->Dlo, g->ldf, g->Dfh, g->Dfl,
+                                       close); note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
+}
+
 // Upper-triangle tiles of the FP32 pair D: block (x, y) fills 256 entries of tile row
 // I = y; entry q of the row's run of tiles is tile J = I + q / 4096, element q % 4096.
 __global__ void k_build_dsym(const atom64_t *__restrict__ atom, const double *__restrict__ eta, int64_t n,
@@ -211,9 +263,25 @@ __global__ void k_rhs(int64_t n, const double *__restrict__ xyz, const int64_t *
     }
 }
 
+// BEM: R[i][d] = -E0 a_i (n_i . dir_d), element i's area times the normal derivative of
+// phi = -E0 dir_d . r (Eq. 21 with the sign that makes q the physical charge).
+__global__ void k_rhs_bem(int64_t n, const elem64_t *__restrict__ el, int ndir, const double *__restrict__ dirs,
+                          double E0, double *__restrict__ R) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const elem64_t e = el[i];
+    for (int d = 0; d < ndir; ++d)
+        R[i * ndir + d] = -E0 * e.area * (e.nx * dirs[3 * d] + e.ny * dirs[3 * d + 1] + e.nz * dirs[3 * d + 2]);
+}
+
 int launch_rhs(const wfq_geom *g, int ndir, const double *dirs_dev, double E0, double *R,
                cudaStream_t s) {
     int64_t n = g->n;
+    if (g->op == OP_BEM) {
+        k_rhs_bem<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, g->elem, ndir, dirs_dev, E0, R); note_launch();
+        WFQ_CUDA(cudaGetLastError());
+        return WFQ_OK;
+    }
     k_rhs<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, g->xyz, g->rowptr, g->col, g->val64, ndir,
                                                      dirs_dev, E0, R); note_launch();
     WFQ_CUDA(cudaGetLastError());

@@ -484,13 +484,11 @@ __global__ void k_backsolve(int64_t na, int jlast, GmresDev st, double2 *__restr
     }
 }
 
-__global__ void k_set_z(int64_t cc, const double *__restrict__ col_omega, double n0, double tau,
+__global__ void k_set_z(int64_t cc, const double *__restrict__ col_omega, ShiftModel zm,
                         double2 *__restrict__ z) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cc) return;
-    const double w = col_omega[c];
-    const double f = -w / (2.0 * n0 * tau);
-    z[c] = make_double2(f * w * tau, f);
+    z[c] = z_eval(zm, col_omega[c]);
 }
 
 // ------------------------------------------------------------------ shared solver set-up
@@ -547,7 +545,7 @@ struct Common {
         WFQ_CUDA(cudaMemcpyAsync(dirs.ptr, a.dirs, sizeof(double) * 3 * a.ndir, cudaMemcpyHostToDevice, s));
         WFQ_CUDA(cudaMemcpyAsync(omega.ptr, om_c.data(), sizeof(double) * cc, cudaMemcpyHostToDevice, s));
         WFQ_CUDA(cudaMemcpyAsync(coldir.ptr, dir_c.data(), sizeof(int) * cc, cudaMemcpyHostToDevice, s));
-        k_set_z<<<nblocks(cc), 256, 0, s>>>(cc, omega.ptr, g->p.n0, g->p.tau, z.ptr); note_launch();
+        k_set_z<<<nblocks(cc), 256, 0, s>>>(cc, omega.ptr, shift_model(g), z.ptr); note_launch();
         WFQ_CUDA(cudaGetLastError());
         WFQ_TRY(launch_rhs(g, a.ndir, dirs.ptr, a.E0, R.ptr, s));
         k_make_b<<<nblocks(n * cc), 256, 0, s>>>((uint32_t)(n * cc), (uint32_t)cc, a.ndir, coldir.ptr, R.ptr, B.ptr); note_launch();

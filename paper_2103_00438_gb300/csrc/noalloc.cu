@@ -61,6 +61,7 @@ extern "C" int wfq_apply_mixed_noalloc(wfq_geom *g, int64_t ncplx, const double 
     if (!g || !omega || !x || !y) return fail(WFQ_EINVAL, "NULL argument");
     if (ncplx < 1) return fail(WFQ_EINVAL, "ncplx must be >= 1");
     if (!g->Dhi) return fail(WFQ_EUNSUPPORTED, "the mixed apply needs WFQ_STORE_BF16X2");
+    if (g->op != OP_WFQ) return fail(WFQ_EUNSUPPORTED, "wfq_apply_mixed_noalloc takes omega-FQ geometries only");
     for (int64_t c = 0; c < ncplx; ++c)
         if (!std::isfinite(omega[c])) return fail(WFQ_EINVAL, "omega has a non-finite entry");
     const int64_t n = g->n;

@@ -215,7 +215,9 @@ struct wfq_server {
             a.m = head->m;
             a.rel_tol = head->rel_tol;
             a.max_iter = head->max_iter;
-            a.prec = WFQ_PREC_MIXED;
+            // continuations of a BEM batch run in FP64 unless its bf16 planes are stored
+            // (its operator is never regenerated from the coordinates)
+            a.prec = (g->op == OP_BEM && !g->Dhi) ? WFQ_PREC_FP64 : WFQ_PREC_MIXED;
             a.q = q.ptr;
             a.stats = st.data();
             if (use_shifted(g)) {

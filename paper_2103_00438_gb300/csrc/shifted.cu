@@ -630,13 +630,11 @@ __global__ void k_shift_combine(int64_t n, int64_t nc, const double *__restrict_
     q[e] = c_add(a, b);
 }
 
-__global__ void k_shift_z(int64_t nc, const double *__restrict__ col_omega, double n0, double tau,
+__global__ void k_shift_z(int64_t nc, const double *__restrict__ col_omega, ShiftModel zm,
                           double2 *__restrict__ z) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
-    const double w = col_omega[c];   // Eq. 12
-    const double f = -w / (2.0 * n0 * tau);
-    z[c] = make_double2(f * w * tau, f);
+    z[c] = z_eval(zm, col_omega[c]);   // Eq. 12 (omega-FQ) or -Lambda(w) of Eq. 21 (BEM)
 }
 
 // ------------------------------------------------------------------ host
@@ -763,9 +761,13 @@ struct Arnoldi {
         return WFQ_OK;
     }
 
-    // w = (Kbar - P) u
+    // w = (Kbar - P) u; BEM geometries (A = the stored operator itself): w = u
     int sparse(const double *u, double *w) {
         KScope ks(g->ctx, WFQ_KT_SPARSE, s);
+        if (g->op == OP_BEM) {
+            WFQ_CUDA(cudaMemcpyAsync(w, u, sizeof(double) * n * C, cudaMemcpyDeviceToDevice, s));
+            return WFQ_OK;
+        }
         const bool wide = g->nnz > 128 * n;   // long rows: a full warp per row
         const unsigned blocks = nblk(n * (wide ? 32 : 8));
         for (int d0 = 0; d0 < C; d0 += 4) {
@@ -851,7 +853,7 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     WFQ_CUDA(cudaMemcpyAsync(dirs.ptr, a.dirs, sizeof(double) * 3 * C, cudaMemcpyHostToDevice, s));
     WFQ_CUDA(cudaMemcpyAsync(om.ptr, om_h.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, s));
     WFQ_CUDA(cudaMemsetAsync(H.ptr, 0, sizeof(double) * C * m * (m + 1), s));
-    k_shift_z<<<nblk(nc), 256, 0, s>>>(nc, om.ptr, g->p.n0, g->p.tau, z.ptr); note_launch();
+    k_shift_z<<<nblk(nc), 256, 0, s>>>(nc, om.ptr, shift_model(g), z.ptr); note_launch();
 
     // v_0 = R_d / ||R_d||
     WFQ_TRY(launch_rhs(g, (int)C, dirs.ptr, a.E0, R.ptr, s));

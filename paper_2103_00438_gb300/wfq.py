@@ -20,7 +20,8 @@ STORE_FP64, STORE_BF16X2, STORE_F32X2, STORE_F32X2_SYM = 1, 2, 4, 8
 PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2
 
 # every symbol include/wfq.h declares
-EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry", "wfq_free_geometry",
+EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry",
+           "wfq_build_bem_geometry", "wfq_free_geometry",
            "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_gmres_shifted", "wfq_solve_qmr",
            "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc",
            "wfq_server_create", "wfq_server_submit", "wfq_server_poll", "wfq_server_destroy"]
@@ -36,6 +37,14 @@ class WfqError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("eta", "d_fermi", "s_fermi", "r0", "area", "n0", "tau", "cutoff_eps")]
+
+    @classmethod
+    def from_dict(cls, p):
+        return cls(*[float(p[k]) for k, _ in cls._fields_])
+
+
+class BemParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("eps_out", "eps_inf", "omega_p", "gamma")]
 
     @classmethod
     def from_dict(cls, p):
@@ -65,6 +74,8 @@ def load(path: str | None = None):
     L.wfq_kernel_launches.restype = ctypes.c_int64
     L.wfq_build_geometry.argtypes = [_P, I64, _P, _P, ctypes.POINTER(Params), ctypes.c_uint32,
                                      ctypes.POINTER(_P)]
+    L.wfq_build_bem_geometry.argtypes = [_P, I64, _P, _P, _P, _P, ctypes.POINTER(BemParams), ctypes.c_uint32,
+                                         ctypes.POINTER(_P)]
     L.wfq_free_geometry.argtypes = [_P]
     L.wfq_geometry_info.argtypes = [_P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
     L.wfq_apply.argtypes = [_P, I64, _P, _P, _P, INT, _P]
@@ -286,6 +297,39 @@ class Geometry:
         out = np.empty((ncols, 3), dtype=np.complex128)
         _check(_lib.wfq_polarizability(self.h, ncols, pq, float(E0), _ptr(out), _stream_handle(stream)))
         return out
+
+
+
+class BemGeometry(Geometry):
+    """A surface for the continuum BEM operator (wfq_build_bem_geometry): collocation
+    points, outward unit normals, element areas and mean curvatures (None: flat
+    elements), and the Drude parameters (eps_out, eps_inf, omega_p, gamma).  Every
+    Geometry call applies; solve_qmr is not available."""
+
+    def __init__(self, ctx: Context, xyz, normal, area, curvature, bem: dict, store: int = STORE_FP64):
+        xyz = _host_f64(xyz)
+        if xyz.ndim != 2 or xyz.shape[1] != 3:
+            raise ValueError("xyz must be (n, 3)")
+        n = len(xyz)
+        normal = _host_f64(normal)
+        area = _host_f64(area)
+        if normal.shape != (n, 3) or area.shape != (n,):
+            raise ValueError("normal must be (n, 3) and area (n,)")
+        curv = None
+        if curvature is not None:
+            curv = _host_f64(curvature)
+            if curv.shape != (n,):
+                raise ValueError("curvature must be (n,)")
+        self.ctx = ctx
+        self.n = n
+        self.params = dict(bem)
+        self._xyz = xyz
+        p = BemParams.from_dict(bem)
+        h = _P()
+        self.h = None
+        _check(_lib.wfq_build_bem_geometry(ctx.h, n, _ptr(xyz), _ptr(normal), _ptr(area), _ptr(curv),
+                                           ctypes.byref(p), int(store), ctypes.byref(h)))
+        self.h = h
 
 
 class Server:
