@@ -115,22 +115,36 @@ def test_bem_shifted_gmres_columns_match_lu(W, ctx, bem, S, surf, store):
 
 def test_bem_shifted_gmres_iterates_match_oracle_gmres(W, ctx, orc, bem, S, surf):
     """After k Arnoldi steps each column holds the k-step GMRES iterate of its own system,
-    computed by the oracle's GMRES on the oracle's dense A."""
+    computed by the oracle's GMRES on the oracle's dense A.
+
+    Tolerance: 1e-10 relative, or, where the k-step least-squares problem is ill
+    conditioned, 1000 times the oracle iterate's own change when every entry of A is
+    perturbed by 2^-48 relative (seeded signs) -- the rounding level of the double-float
+    products; the factor covers the per-row sum of |A_ij x_j| of those products (up to
+    sqrt(N) ~ 40 above the random-sign model) and the other rounding orders (real Arnoldi of
+    A with CGS2 and shifted Givens, against complex Arnoldi of A - zI with MGS)."""
     s, A, m = surf
     g = _geom(W, ctx, s, m, W.STORE_FP64 | W.STORE_F32X2)
     om = S.ev([2.2, 3.4])
     dirs = np.array([[1.0, 0, 0], [0, 0, 1.0]])
     op = orc.Operator.dense(A)
+    sign = np.where(np.random.default_rng(48).random(A.shape) < 0.5, -1.0, 1.0)
+    op_pert = orc.Operator.dense(A * (1.0 + 2.0 ** -48 * sign))
     for k in (1, 4, 10):
         q, st, status = g.solve_gmres_shifted(om, dirs, m_max=k, rel_tol=1e-14, max_iter=k, prec=W.PREC_FP64)
         assert status == "WFQ_ENOCONV"
         for f in range(len(om)):
+            z = bem.z_of_omega(om[f], m)
             for d in range(2):
                 c = f * 2 + d
                 assert st[c]["iters"] == k
                 R = bem.rhs(s["normal"], s["area"], dirs[d]).astype(complex)
-                qo, _ = op.gmres(bem.z_of_omega(om[f], m), R, restart=0, rel_tol=1e-300, max_iter=k)
-                assert np.linalg.norm(q[:, c] - qo) <= 1e-10 * np.linalg.norm(qo), (k, f, d)
+                qo, _ = op.gmres(z, R, restart=0, rel_tol=1e-300, max_iter=k)
+                qp, _ = op_pert.gmres(z, R, restart=0, rel_tol=1e-300, max_iter=k)
+                sens = np.linalg.norm(qp - qo) / np.linalg.norm(qo)
+                dev = np.linalg.norm(q[:, c] - qo) / np.linalg.norm(qo)
+                print(f"k={k} f={f} d={d}: |q - q_oracle| / |q| = {dev:.2e}, oracle sensitivity {sens:.2e}")
+                assert dev <= max(1e-10, 1e3 * sens), (k, f, d, dev, sens)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
