@@ -300,6 +300,14 @@ int wfq_server_submit(wfq_server *sv, wfq_geom *g, int64_t nfreq, const double *
         if (!std::isfinite(omega[f])) return fail(WFQ_EINVAL, "non-finite omega");
         if (omega[f] == 0.0) return fail(WFQ_ESINGULAR, "omega = 0: z(0) = 0 and A is singular");
     }
+    if (g->op == OP_BEM) {
+        const ShiftModel zm = shift_model(g);
+        for (int64_t f = 0; f < nfreq; ++f) {
+            const double2 z = z_eval(zm, omega[f]);
+            if (!(std::isfinite(z.x) && std::isfinite(z.y)))
+                return fail(WFQ_EINVAL, "eps_in(omega) = eps_out: Lambda(omega) is infinite");
+        }
+    }
     if (g->ctx != sv->ctx) return fail(WFQ_EINVAL, "geometry belongs to another context");
     const int64_t cols = nfreq * ndir;
     if (cols > sv->max_cols) return fail(WFQ_EINVAL, "request has more columns than the server's batch limit");

@@ -185,6 +185,36 @@ def test_bem_sphere_polarizability_on_gpu_tends_to_closed_form(W, ctx, S):
         assert abs(al[f] / ex - 1.0) < 1.2 / np.sqrt(n), (f, al[f], ex)
 
 
+def test_bem_geometry_through_the_server(W, ctx, bem, S, surf):
+    """BEM requests mixed with omega-FQ requests in the request server: each BEM column
+    meets the acceptance bar against its own oracle LU solve."""
+    s, A, m = surf
+    gb = _geom(W, ctx, s, m, W.STORE_FP64)
+    gw = W.Geometry(ctx, S.honeycomb_flake(8), S.carbon_params(1.51), store=W.STORE_F32X2)
+    sv = W.Server(ctx, nworkers=2, budget_bytes=8 << 30, max_columns=48)
+    reqs = [(gb, S.ev([2.3, 3.3]), np.eye(3)[:2]), (gw, S.ev([0.4, 0.9]), np.eye(3)[:1]),
+            (gb, S.ev([4.0]), np.eye(3)[2:]), (gb, S.ev([2.8, 3.9]), np.eye(3))]
+    ids = [sv.submit(g, om, d, rel_tol=1e-8) for g, om, d in reqs]
+    res = [sv.poll(i, wait=True) for i in ids]
+    sv.close()
+    for (g, om, d), r in zip(reqs, res):
+        assert r["status"] == "WFQ_OK", r["stats"]
+        if g is gw:
+            continue
+        al = g.polarizability(r["q"])
+        for f in range(len(om)):
+            z = bem.z_of_omega(om[f], m)
+            for k in range(len(d)):
+                c = f * len(d) + k
+                R = bem.rhs(s["normal"], s["area"], d[k]).astype(complex)
+                a_ref = bem.alpha(s["xyz"], bem.solve(A, z, R))
+                assert np.abs(al[c] - a_ref).max() <= 1e-6 * np.abs(a_ref).max(), (f, k)
+                qc = r["q"][:, c]
+                assert np.linalg.norm(R - (A @ qc - z * qc)) <= 1e-8 * np.linalg.norm(R)
+    gw.close()
+    gb.close()
+
+
 def test_bem_errors(W, ctx, S, surf):
     s, A, m = surf
     g = _geom(W, ctx, s, m, W.STORE_FP64)
