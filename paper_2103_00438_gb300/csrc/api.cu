@@ -473,14 +473,18 @@ int wfq_build_bem_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const dou
         if ((rc = galloc(g, &g->Dfh, (size_t)n * g->ldf))) return bail(rc);
         if ((rc = galloc(g, &g->Dfl, (size_t)n * g->ldf))) return bail(rc);
     }
+    // device flag of the build kernel: two elements closer than 1e-8 bohr (freed below)
     int *close = nullptr;
-    if ((rc = galloc(g, &close, 1))) return bail(rc);
-    g->bytes -= sizeof(int);
+    cudaError_t e = cudaMalloc(&close, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(WFQ_ENOMEM, std::string("BEM build flag: ") + cudaGetErrorString(e)));
+    }
     auto done = [&](int code) {
         cudaFree(close);
         return code == WFQ_OK ? WFQ_OK : bail(code);
     };
-    cudaError_t e = cudaMemcpy(g->xyz, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(g->xyz, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->elem, el.data(), sizeof(elem64_t) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(g->rowptr, 0, sizeof(int64_t) * (n + 1));
     if (e == cudaSuccess) e = cudaMemset(close, 0, sizeof(int));

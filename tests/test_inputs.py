@@ -45,3 +45,57 @@ def test_flake_counts_and_bond_length(S, n_rings):
     from scipy.spatial import cKDTree
     dmin = cKDTree(xyz).query(xyz, k=2)[0][:, 1].min() / S.BOHR_PER_ANGSTROM
     assert abs(dmin - 1.42) < 1e-9
+
+
+@pytest.mark.parametrize("a,b", [(40.0, 40.0), (60.0, 30.0), (25.0, 50.0)])
+def test_spheroid_surface_geometry(S, a, b):
+    """The BEM surface recipe: points on the spheroid, unit outward normals along the
+    gradient of the implicit surface, areas summing to the exact spheroid area, and the
+    mean curvature 1/R on a sphere and half the divergence of the unit normal field
+    everywhere."""
+    n = 4000
+    s = S.spheroid_surface(n, a, b)
+    x, y, z = s["xyz"].T
+    assert np.abs((x * x + y * y) / b ** 2 + z * z / a ** 2 - 1.0).max() < 1e-12
+    nrm = s["normal"]
+    assert np.abs(np.linalg.norm(nrm, axis=1) - 1.0).max() < 1e-12
+    grad = np.stack([x / b ** 2, y / b ** 2, z / a ** 2], axis=1)
+    grad /= np.linalg.norm(grad, axis=1)[:, None]
+    assert np.abs(nrm - grad).max() < 1e-12
+    if a == b:
+        exact = 4.0 * np.pi * a * a
+    elif a > b:      # prolate
+        e = np.sqrt(1.0 - b * b / (a * a))
+        exact = 2.0 * np.pi * b * b * (1.0 + a / (b * e) * np.arcsin(e))
+    else:            # oblate
+        e = np.sqrt(1.0 - a * a / (b * b))
+        exact = 2.0 * np.pi * b * b * (1.0 + (1.0 - e * e) / e * np.arctanh(e))
+    assert abs(s["area"].sum() / exact - 1.0) < 1e-5
+    assert np.all(s["area"] > 0)
+    H = s["curvature"]
+    if a == b:
+        assert np.abs(H - 1.0 / a).max() < 1e-12
+    # mean curvature = half the divergence of the unit normal field grad F / |grad F| of the
+    # implicit surface F = (x^2 + y^2) / b^2 + z^2 / a^2, by central differences
+    def unit_grad(p):
+        g = np.stack([p[:, 0] / b ** 2, p[:, 1] / b ** 2, p[:, 2] / a ** 2], axis=1)
+        return g / np.linalg.norm(g, axis=1)[:, None]
+    h = 1e-4 * min(a, b)
+    div = np.zeros(n)
+    for k in range(3):
+        dp = np.zeros(3)
+        dp[k] = h
+        div += (unit_grad(s["xyz"] + dp)[:, k] - unit_grad(s["xyz"] - dp)[:, k]) / (2.0 * h)
+    assert np.abs(H / (0.5 * div) - 1.0).max() < 1e-6
+    # the same call gives the same mesh (no seed: the lattice is deterministic)
+    assert np.array_equal(S.spheroid_surface(n, a, b)["xyz"], s["xyz"])
+
+
+def test_drude_metal_resonance_in_band(S):
+    m = S.drude_metal_params()
+    wl = S.workload("bem_spheroid30k")
+    # sphere dipole resonance eps_in = -2: w = wp / sqrt(eps_inf + 2 eps_out) = 3.41 eV
+    w_f = m["omega_p"] / np.sqrt(m["eps_inf"] + 2.0 * m["eps_out"]) * S.HARTREE_EV
+    assert abs(w_f - 3.406) < 1e-3
+    assert wl["omega"][0] < S.ev(w_f) < wl["omega"][-1]
+    assert len(wl["omega"]) == 64 and wl["surface"]["xyz"].shape == (30000, 3)
