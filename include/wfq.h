@@ -15,6 +15,10 @@
  *     z(w) = -(w / (2 n0 tau)) (w tau + i)                   (Eq. 12)
  *     R_i = sum_j (V_i - V_j) Kbar_ij, V_i = -E0 (r_i . k)   (Eq. 13, Eq. 2)
  *
+ * The same machinery also solves the continuum (BEM) operator of Section 2.3 (Eq. 21,
+ * Eq. 22), which has the same form -- a real frequency-independent matrix with a uniform
+ * complex shift -- on geometries built by wfq_build_bem_geometry.
+ *
  * Units are atomic units throughout (bohr, hartree, a.u. of time).
  *
  * Conventions shared by every entry point

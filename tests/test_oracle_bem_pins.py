@@ -149,3 +149,26 @@ def test_rhs_is_normal_flux_of_the_field(bem, S):
         R = bem.rhs(s["normal"], s["area"], k, E0=0.5)
         # element i: -E0 a_i cos(angle between n_i and k); on a sphere n_i = r_i / R
         assert np.allclose(R, -0.5 * s["area"] * (s["xyz"] @ k) / 10.0, rtol=0, atol=1e-14)
+
+
+def test_two_spheres_couple_as_point_dipoles(bem, S):
+    # Two equal spheres a distance d apart, each much smaller than d, interact through
+    # their induced dipoles: along the axis alpha_pair = 2 alpha / (1 - 2 alpha / d^3),
+    # across it 2 alpha / (1 + alpha / d^3) (coupled point dipoles; the next multipole
+    # corrections are O((R/d)^5)).  With alpha the same mesh's single-sphere value, the
+    # collocation error cancels and what is left checks the operator's far blocks: the
+    # field of one body's charges at the other's elements, with its sign.
+    n, R, d = 1000, 10.0, 50.0
+    s = S.spheroid_surface(n, R, R)
+    two = {k: np.concatenate([v, v]) for k, v in s.items()}
+    two["xyz"] = np.concatenate([s["xyz"] - [0.0, 0.0, d / 2], s["xyz"] + [0.0, 0.0, d / 2]])
+    A1 = bem.a_matrix(s["xyz"], s["normal"], s["area"], s["curvature"])
+    A2 = bem.a_matrix(two["xyz"], two["normal"], two["area"], two["curvature"])
+    z = complex(-2.0 * math.pi * (1.0 + 5.0) / (1.0 - 5.0))     # static dielectric, eps_in = 5
+    for k, g in ((2, 2.0), (0, -1.0)):
+        kd = np.eye(3)[k]
+        a1 = bem.alpha(s["xyz"], bem.solve(A1, z, bem.rhs(s["normal"], s["area"], kd)))[k]
+        a2 = bem.alpha(two["xyz"], bem.solve(A2, z, bem.rhs(two["normal"], two["area"], kd)))[k]
+        pred = 2.0 * a1 / (1.0 - g * a1 / d ** 3)
+        assert abs(pred / (2.0 * a1) - 1.0) > 4e-3            # the coupling is visible ...
+        assert abs(a2 / pred - 1.0) < 1e-4, (k, a2, pred)     # ... and has the dipole form
