@@ -95,7 +95,7 @@ typedef struct {
                                 with Np = N rounded up to 128: the tensor-core path */
 #define WFQ_STORE_F32X2  4u  /* D as two FP32 planes hi + lo (hi = fl32(D), lo = fl32(D - hi):
                                 48 significant bits), N*Nq*8 bytes with Nq = N rounded up to
-                                4: double-float products on the FP32 pipes without FP64
+                                128 (512-byte rows, zero past column N): double-float products on the FP32 pipes without FP64
                                 arithmetic (the shifted solver's operator, the refinement
                                 residual) */
 #define WFQ_STORE_F32X2_SYM 8u  /* the same FP32 hi + lo pairs for the upper triangle only
@@ -169,7 +169,7 @@ int wfq_profile(wfq_ctx *ctx, int enable);
 /* Launches, summed device milliseconds and summed work of kernel class `kind` (WFQ_KT_*).
  * Work: WFQ_KT_GEMM_MIXED -- tensor flops of the three bf16 products, 6 N^2 C per launch
  * (C = real columns of that launch); WFQ_KT_DAPPLY_FP64 -- 2 N^2 C flops; WFQ_KT_DGEMV_DF --
- * bytes of D read (8 N Nq for the FP32 pair planes, 8 N^2 for the FP64 D); others 0.
+ * algorithmic bytes of D read, 8 N^2 (the entries; padding columns not counted); others 0.
  * Any out-pointer may be NULL. */
 int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms, double *work);
 

@@ -318,7 +318,7 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     g->ctx = ctx;
     g->n = n;
     g->npad = round_up(n, kTilePad);
-    g->ldf = round_up(n, 4);
+    g->ldf = round_up(n, 128);
     g->p = *p;
     g->store = store;
     g->nnz = rowptr[n];
@@ -452,7 +452,7 @@ int wfq_build_bem_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const dou
     g->op = OP_BEM;
     g->n = n;
     g->npad = round_up(n, kTilePad);
-    g->ldf = round_up(n, 4);
+    g->ldf = round_up(n, 128);
     g->bem = *p;
     g->store = store;
     g->nnz = 0;

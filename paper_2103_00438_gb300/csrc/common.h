@@ -170,7 +170,7 @@ struct wfq_geom {
     __nv_bfloat16 *Dlo = nullptr;
     float *Dfh = nullptr;       // n x ldf row-major: fl32(D_ij) (zero for j >= n)
     float *Dfl = nullptr;       // n x ldf row-major: fl32(D_ij - Dfh_ij)
-    int64_t ldf = 0;            // n rounded up to 4 (16-byte rows)
+    int64_t ldf = 0;            // n rounded up to 128 (512-byte rows; the GEMV steps 128 columns)
     // upper-triangle 64 x 64 tiles of the FP32 pairs (WFQ_STORE_F32X2_SYM)
     float *Dsym = nullptr;      // tile t(I, J): 4096 hi then 4096 lo floats, row-major
     int64_t sym_nt = 0;         // tiles per side, ceil(n / 64)

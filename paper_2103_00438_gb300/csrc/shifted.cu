@@ -82,6 +82,21 @@ __global__ void __launch_bounds__(GV_WARPS * 32, MINB) k_dgemv_df(int64_t n, int
     __shared__ __align__(16) float sxl[C][GV_CHUNK];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = ((int64_t)blockIdx.x * GV_WARPS + warp) * ROWS;
+    // FP32 planes (PL): rows of ld floats, ld a multiple of 128, zero past column n, so a
+    // 128-column step that starts below n lies inside the row and needs no column check;
+    // rows past n read the last row (their results are dropped).  This lane's float4 of
+    // each row, as a pointer advanced by the step's float4 index.
+    const float4 *rowh[ROWS], *rowl[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        if constexpr (PL) {
+            const int64_t i = row0 + r, ic = i < n ? i : n - 1;
+            rowh[r] = reinterpret_cast<const float4 *>(Fh + ic * ld) + lane;
+            rowl[r] = reinterpret_cast<const float4 *>(Fl + ic * ld) + lane;
+        } else {
+            rowh[r] = rowl[r] = nullptr;
+        }
+    }
     float sh[ROWS][C], sl[ROWS][C];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r)
@@ -103,15 +118,21 @@ __global__ void __launch_bounds__(GV_WARPS * 32, MINB) k_dgemv_df(int64_t n, int
             float4 dh[TB][ROWS], dl[TB][ROWS];
 #pragma unroll
             for (int t = 0; t < TB; ++t) {
-                const int64_t j = j0 + (t0 + t) * 128 + lane * 4;
+                const int tt = t0 + t;
+                const int64_t j = j0 + tt * 128 + lane * 4;
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     const int64_t i = row0 + r;
-                    if (i >= n || j >= n) {
+                    if constexpr (PL) {
+                        if (tt < tend) {   // warp-uniform: the last chunk may end inside the TB group
+                            const int64_t q = (j0 >> 2) + tt * 32;
+                            dh[t][r] = __ldg(rowh[r] + q);
+                            dl[t][r] = __ldg(rowl[r] + q);
+                        } else {
+                            dh[t][r] = dl[t][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    } else if (i >= n || j >= n) {
                         dh[t][r] = dl[t][r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    } else if (PL) {
-                        dh[t][r] = __ldg(reinterpret_cast<const float4 *>(Fh + i * ld + j));
-                        dl[t][r] = __ldg(reinterpret_cast<const float4 *>(Fl + i * ld + j));
                     } else {
                         const double *row = D64 + i * n;
                         float h[4], l[4];
@@ -745,7 +766,7 @@ struct Arnoldi {
             WFQ_CUDA(cudaGetLastError());
             return WFQ_OK;
         }
-        const double dbytes = 8.0 * (double)n * (double)(g->Dfh ? g->ldf : n);
+        const double dbytes = 8.0 * (double)n * (double)n;   // algorithmic: the N^2 entries, 8 bytes each
         const bool pl = g->Dfh != nullptr;
         for (int d0 = 0; d0 < C; d0 += 4) {
             const int cg = std::min(4, C - d0);
