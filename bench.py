@@ -77,8 +77,8 @@ def store_for(name, wfq, solver="gmres"):
 
 
 # DRAM bytes per stored D entry that ncu measured for one k_dgemv_df launch (cnt8k, N = 8200:
-# 543.5 MB read + written for 8200 x 8200 entries of the FP32 pair planes).
-DGEMV_DRAM_BYTES_PER_ENTRY = 543.5e6 / (8200.0 * 8200.0)
+# 549.5 MB read + written for 8200 x 8320 stored entries of the FP32 pair planes).
+DGEMV_DRAM_BYTES_PER_ENTRY = 549.5e6 / (8200.0 * 8320.0)
 
 # FP32 lane-instructions per second of the whole GPU: 152 SMs x 128 lanes x 2070 MHz.
 FP32_LANE_OPS_PER_S = 152 * 128 * 2.07e9
