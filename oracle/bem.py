@@ -30,7 +30,9 @@ library solves it in the same form as the omega-FQ system, (A - zI) q = R, with:
 Pins (tests/test_oracle_bem_pins.py): the sphere's multipole eigenvalues
 2 pi / (2l + 1); Gauss's law (column sums of A tend to 2 pi on any closed surface);
 the quasi-static polarizabilities of a sphere and of a prolate spheroid
-(depolarization factors); the resonance condition z(w_F) = 2 pi / 3; a real spectrum.
+(depolarization factors); the resonance condition z(w_F) = 2 pi / 3; a real spectrum;
+passivity (Im eps_in > 0, eps_in equal to eps_inf + 4 pi i sigma / w for the Drude
+conductivity in the time convention of Eq. 5, Im alpha_kk >= 0).
 """
 import math
 

@@ -25,41 +25,47 @@ OP_DENSE_A, OP_STORED_D, OP_OTF_D = 0, 1, 2
 
 
 def lib():
+    """The oracle library built from oracle/wfq_oracle.c (built on first use)."""
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        L.orc_widths.argtypes = [_I64, _P, _P]
-        L.orc_d_entry.argtypes = [_P, _P, _I64, _I64]
-        L.orc_d_entry.restype = _D
-        L.orc_d_matrix.argtypes = [_I64, _P, _P, _P]
-        L.orc_fermi.argtypes = [_D, _D, _D, _D]
-        L.orc_fermi.restype = _D
-        L.orc_kbar_entry.argtypes = [_D, _D, _D, _D, _D]
-        L.orc_kbar_entry.restype = _D
-        L.orc_kbar_matrix.argtypes = [_I64, _P, _D, _D, _D, _D, _P]
-        L.orc_kbar_csr.argtypes = [_I64, _P, _D, _D, _D, _D, _D, _P, _P, _P]
-        L.orc_kbar_csr.restype = _I64
-        L.orc_z.argtypes = [_D, _D, _D, _P, _P]
-        L.orc_rhs_csr.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _P]
-        L.orc_rhs_dense.argtypes = [_I64, _P, _P, _P, _D, _P]
-        L.orc_a_matrix.argtypes = [_I64, _P, _P, _P]
-        L.orc_apply.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _P]
-        L.orc_d_matvec.argtypes = [_INT, _I64, _P, _P, _P, _P, _P]
-        L.orc_lu_solve.argtypes = [_I64, _P, _D, _D, _P, _P]
-        L.orc_lu_solve.restype = _INT
-        L.orc_gmres.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _INT, _D,
-                                _INT, _P, _P]
-        L.orc_gmres.restype = _INT
-        L.orc_qmr.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _D, _D, _P, _D, _INT, _P, _P]
-        L.orc_qmr.restype = _INT
-        L.orc_alpha.argtypes = [_I64, _P, _P, _D, _P]
-        L.orc_residual_norm.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _P]
-        L.orc_residual_norm.restype = _D
-        L.orc_vdot.argtypes = [_I64, _P, _P, _P]
-        L.orc_apply_rows.argtypes = [_I64, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _I64, _P, _P, _P]
-        _lib = L
+        _lib = load(_build.build())
     return _lib
+
+
+def load(path):
+    """Load and bind a build of the oracle's C source at `path` (tests compile copies of
+    the source with a planted mistake to show that a pin catches it)."""
+    L = ctypes.CDLL(path)
+    L.orc_widths.argtypes = [_I64, _P, _P]
+    L.orc_d_entry.argtypes = [_P, _P, _I64, _I64]
+    L.orc_d_entry.restype = _D
+    L.orc_d_matrix.argtypes = [_I64, _P, _P, _P]
+    L.orc_fermi.argtypes = [_D, _D, _D, _D]
+    L.orc_fermi.restype = _D
+    L.orc_kbar_entry.argtypes = [_D, _D, _D, _D, _D]
+    L.orc_kbar_entry.restype = _D
+    L.orc_kbar_matrix.argtypes = [_I64, _P, _D, _D, _D, _D, _P]
+    L.orc_kbar_csr.argtypes = [_I64, _P, _D, _D, _D, _D, _D, _P, _P, _P]
+    L.orc_kbar_csr.restype = _I64
+    L.orc_z.argtypes = [_D, _D, _D, _P, _P]
+    L.orc_rhs_csr.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _P]
+    L.orc_rhs_dense.argtypes = [_I64, _P, _P, _P, _D, _P]
+    L.orc_a_matrix.argtypes = [_I64, _P, _P, _P]
+    L.orc_apply.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _P]
+    L.orc_d_matvec.argtypes = [_INT, _I64, _P, _P, _P, _P, _P]
+    L.orc_lu_solve.argtypes = [_I64, _P, _D, _D, _P, _P]
+    L.orc_lu_solve.restype = _INT
+    L.orc_gmres.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _INT, _D,
+                            _INT, _P, _P]
+    L.orc_gmres.restype = _INT
+    L.orc_qmr.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _D, _D, _P, _D, _INT, _P, _P]
+    L.orc_qmr.restype = _INT
+    L.orc_alpha.argtypes = [_I64, _P, _P, _D, _P]
+    L.orc_residual_norm.argtypes = [_INT, _I64, _P, _P, _P, _P, _P, _P, _P, _D, _D, _P, _P]
+    L.orc_residual_norm.restype = _D
+    L.orc_vdot.argtypes = [_I64, _P, _P, _P]
+    L.orc_apply_rows.argtypes = [_I64, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _I64, _P, _P, _P]
+    return L
 
 
 def _ptr(a):
@@ -245,12 +251,13 @@ class Operator:
         return q, {"status": st, "iters": int(out[0]), "rel_residual": out[1],
                    "restarts": int(out[2])}
 
-    def qmr(self, z, R, rel_tol=1e-12, max_iter=1000):
-        """Section 3 J-symmetric QMR-from-BCG (J = D), q0 = 0.  Returns (q, info)."""
+    def qmr(self, z, R, rel_tol=1e-12, max_iter=1000, library=None):
+        """Section 3 J-symmetric QMR-from-BCG (J = D), q0 = 0.  Returns (q, info).
+        `library` runs another build of the oracle's source (see `load`)."""
         R = _c128(R)
         q = np.zeros(self.n, dtype=np.complex128)
         out = np.zeros(3)
-        st = lib().orc_qmr(self.kind, self.n, _ptr(self.D), _ptr(self.xyz), _ptr(self.eta),
+        st = (library or lib()).orc_qmr(self.kind, self.n, _ptr(self.D), _ptr(self.xyz), _ptr(self.eta),
                            _ptr(self.rowptr), _ptr(self.col), _ptr(self.val), z.real, z.imag,
                            _ptr(R), float(rel_tol), int(max_iter), _ptr(q), _ptr(out))
         return q, {"status": st, "iters": int(out[0]), "rel_residual": out[1]}

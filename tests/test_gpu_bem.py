@@ -118,11 +118,11 @@ def test_bem_shifted_gmres_iterates_match_oracle_gmres(W, ctx, orc, bem, S, surf
     computed by the oracle's GMRES on the oracle's dense A.
 
     Tolerance: 1e-10 relative, or, where the k-step least-squares problem is ill
-    conditioned, 1000 times the oracle iterate's own change when every entry of A is
+    conditioned, 30 times the oracle iterate's own change when every entry of A is
     perturbed by 2^-48 relative (seeded signs) -- the rounding level of the double-float
-    products; the factor covers the per-row sum of |A_ij x_j| of those products (up to
-    sqrt(N) ~ 40 above the random-sign model) and the other rounding orders (real Arnoldi of
-    A with CGS2 and shifted Givens, against complex Arnoldi of A - zI with MGS)."""
+    products.  The largest ratio measured is 10 (3.4 eV, field z, k = 10: 2.6e-10 against a
+    sensitivity of 2.6e-11); the factor 30 leaves 3x for the other rounding orders (real
+    Arnoldi of A with CGS2 and shifted Givens, against complex Arnoldi of A - zI with MGS)."""
     s, A, m = surf
     g = _geom(W, ctx, s, m, W.STORE_FP64 | W.STORE_F32X2)
     om = S.ev([2.2, 3.4])
@@ -144,7 +144,7 @@ def test_bem_shifted_gmres_iterates_match_oracle_gmres(W, ctx, orc, bem, S, surf
                 sens = np.linalg.norm(qp - qo) / np.linalg.norm(qo)
                 dev = np.linalg.norm(q[:, c] - qo) / np.linalg.norm(qo)
                 print(f"k={k} f={f} d={d}: |q - q_oracle| / |q| = {dev:.2e}, oracle sensitivity {sens:.2e}")
-                assert dev <= max(1e-10, 1e3 * sens), (k, f, d, dev, sens)
+                assert dev <= max(1e-10, 30.0 * sens), (k, f, d, dev, sens)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

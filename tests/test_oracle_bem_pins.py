@@ -2,10 +2,13 @@
 theory, not against the oracle itself: the sphere's multipole eigenvalues
 2 pi / (2l + 1), Gauss's law on a closed spheroid, the quasi-static polarizabilities
 of a sphere and of a prolate spheroid (depolarization factors), the resonance
-condition eps_in = -2 eps_out, and a real spectrum.  The discretisation error of
+condition eps_in = -2 eps_out, a real spectrum, and passivity of the lossy particle
+(Im eps_in > 0 with eps_in rebuilt from the Drude conductivity in the time convention
+of the paper's Eq. 5, Im alpha_kk >= 0).  The discretisation error of
 one-point collocation falls as N^-1/2; each tolerance is a fixed multiple of N^-1/2
 that the correct operator meets and a transposed normal, the other element's area,
-a missing self term or a flipped sign misses.  CPU only."""
+a missing self term or a flipped sign misses; a flipped damping sign fails the
+passivity pin.  CPU only."""
 import math
 
 import numpy as np
@@ -172,3 +175,61 @@ def test_two_spheres_couple_as_point_dipoles(bem, S):
         pred = 2.0 * a1 / (1.0 - g * a1 / d ** 3)
         assert abs(pred / (2.0 * a1) - 1.0) > 4e-3            # the coupling is visible ...
         assert abs(a2 / pred - 1.0) < 1e-4, (k, a2, pred)     # ... and has the dipole form
+
+
+def _eps_from_drude_conductivity(omega, m):
+    """The particle's permittivity rebuilt from its Drude conductivity in the time
+    convention fixed by the paper's Drude factor 2 n0 / (1/tau - i w) (Eq. 5, Eq. 9):
+    sigma(w) = (wp^2 / 4 pi) / (gamma - i w) and eps = eps_inf + 4 pi i sigma(w) / w."""
+    sigma = m["omega_p"] ** 2 / (4.0 * math.pi) / (m["gamma"] - 1j * omega)
+    return m["eps_inf"] + 4j * math.pi * sigma / omega
+
+
+def _passivity_failures(bem, S):
+    """Where a lossy particle (gamma > 0) is not passive: Im eps_in <= 0, eps_in off the
+    conductivity form above, or a negative absorption Im alpha_kk of the sphere or of the
+    2:1 spheroid (three frequencies, field along and across the axis)."""
+    fails = []
+    m = S.drude_metal_params()
+    assert m["gamma"] > 0
+    for w_ev in (0.5, 1.5, 2.5, 3.5, 4.5, 8.0):
+        w = S.ev(w_ev)
+        ei = bem.eps_in(w, m)
+        if not ei.imag > 0:
+            fails.append(("Im eps", w_ev, ei))
+        ref = _eps_from_drude_conductivity(w, m)
+        if abs(ei - ref) > 1e-13 * abs(ref):
+            fails.append(("conductivity form", w_ev, ei, ref))
+    for a, b, n in ((40.0, 40.0, 800), (60.0, 30.0, 1000)):
+        s = S.spheroid_surface(n, a, b)
+        A = bem.a_matrix(s["xyz"], s["normal"], s["area"], s["curvature"])
+        for w_ev in (1.5, 2.5, 4.5):
+            z = bem.z_of_omega(S.ev(w_ev), m)
+            for k in (KX, KZ):
+                q = bem.solve(A, z, bem.rhs(s["normal"], s["area"], k))
+                al = bem.alpha(s["xyz"], q) @ k
+                if not al.imag >= 0:
+                    fails.append(("Im alpha", a, b, w_ev, al))
+    return fails
+
+
+def test_lossy_particle_is_passive(bem, S):
+    # gamma > 0 absorbs: Im eps_in > 0, and Im alpha_kk >= 0 for every shape and field
+    # (the omega-FQ oracle's modal pin asks the same of Im alpha)
+    assert _passivity_failures(bem, S) == []
+
+
+def test_passivity_pin_catches_flipped_damping(bem, S):
+    # a copy of the BEM oracle with w (w - i gamma) in place of w (w + i gamma) -- a gain
+    # medium -- fails the pin above
+    import os
+    src = open(os.path.join(os.path.dirname(bem.__file__), "bem.py")).read()
+    old = 'w * (w + 1j * bem["gamma"])'
+    assert src.count(old) == 1
+    ns = {"__name__": "oracle.bem_planted", "__package__": "oracle"}
+    exec(compile(src.replace(old, 'w * (w - 1j * bem["gamma"])'), "bem_planted", "exec"), ns)
+    planted = type(bem)("bem_planted")
+    planted.__dict__.update(ns)
+    fails = _passivity_failures(planted, S)
+    assert any(f[0] == "Im eps" for f in fails)
+    assert any(f[0] == "Im alpha" for f in fails)

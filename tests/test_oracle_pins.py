@@ -330,6 +330,95 @@ def test_qmr_matches_lu_and_stays_in_krylov_space(orc, S):
         Kr.append(M @ Kr[-1])
 
 
+def _krylov_basis(M, R, k):
+    """Orthonormal basis of K_k(M, R) by Arnoldi with two Gram-Schmidt passes (numpy)."""
+    Q = np.zeros((len(R), k), dtype=complex)
+    Q[:, 0] = R / np.linalg.norm(R)
+    for j in range(1, k):
+        w = M @ Q[:, j - 1]
+        for _ in range(2):
+            w = w - Q[:, :j] @ (Q[:, :j].conj().T @ w)
+        Q[:, j] = w / np.linalg.norm(w)
+    return Q
+
+
+def _qmr_from_bcg_brute_force(M, D, R, kmax):
+    """k-step J-symmetric QMR iterates (J = D, Section 3) built with no Lanczos recurrence.
+
+    BCG: x_k lies in K_k(M, R) and its residual R - M x_k is orthogonal, in the bilinear
+    form u^T D v (no conjugation), to all of K_k(M, R); for M^T D = D M (Eq. 18 with the
+    shift) the shadow space K_k(M^T, D R) is D K_k(M, R), so this is the Petrov-Galerkin
+    condition of BCG with the shadow start D R.  Solved as a dense k x k system.
+
+    QMR from BCG: with Lanczos vectors of unit Euclidean length the QMR iterate is the
+    weighted mean of the BCG iterates x_0 = 0, x_1, ..., x_k with weights proportional to
+    1 / ||r_i||^2 (quasi-residual tau_k^2 = 1 / sum_i ||r_i||^-2)."""
+    xs, inv = [np.zeros_like(R)], [1.0 / np.vdot(R, R).real]
+    out = []
+    for k in range(1, kmax + 1):
+        Q = _krylov_basis(M, R, k)
+        y = np.linalg.solve(Q.T @ D @ M @ Q, Q.T @ D @ R)
+        x = Q @ y
+        r = R - M @ x
+        xs.append(x)
+        inv.append(1.0 / np.vdot(r, r).real)
+        w = np.array(inv) / np.sum(inv)
+        out.append(sum(wi * xi for wi, xi in zip(w, xs)))
+    return out
+
+
+def _qmr_system(orc, S):
+    sysm = orc.System(S.honeycomb_flake(5), _params(S))
+    z = sysm.z(S.ev(0.9))
+    R = sysm.rhs(KX).astype(complex)
+    M = sysm.A - z * np.eye(len(R))
+    return sysm, z, R, M
+
+
+def _qmr_pin_deviation(op, sysm, z, R, M, library=None, kmax=8):
+    ref = _qmr_from_bcg_brute_force(M, sysm.D, R, kmax)
+    dev = []
+    for k in range(1, kmax + 1):
+        xq, info = op.qmr(z, R, rel_tol=1e-300, max_iter=k, library=library)
+        assert info["iters"] == k
+        dev.append(np.linalg.norm(xq - ref[k - 1]) / np.linalg.norm(ref[k - 1]))
+    return max(dev)
+
+
+def test_qmr_iterates_are_smoothed_bcg_iterates(orc, S):
+    # each k-step oracle QMR iterate equals the brute-force BCG + closed-form smoothing
+    sysm, z, R, M = _qmr_system(orc, S)
+    assert _qmr_pin_deviation(sysm.operator(), sysm, z, R, M) <= 1e-9
+
+
+_QMR_PLANTS = {
+    "smoothing weight divided by ||r|| once": (
+        "double wgt = tau2_new / (rn * rn);", "double wgt = tau2_new / rn;"),
+    "quasi-residual not accumulated": (
+        "double tau2_new = 1.0 / (1.0 / tau2 + 1.0 / (rn * rn));",
+        "double tau2_new = 1.0 / (1.0 / (rn * rn));"),
+    "beta inverted": ("cplx beta = rho_new / rho;", "cplx beta = rho / rho_new;"),
+    "conjugating form": ("for (int64_t i = 0; i < n; ++i) s += u[i] * v[i];",
+                         "for (int64_t i = 0; i < n; ++i) s += conj(u[i]) * v[i];"),
+}
+
+
+@pytest.mark.parametrize("plant", sorted(_QMR_PLANTS))
+def test_qmr_pin_catches_planted_mistakes(orc, S, tmp_path, plant):
+    # a copy of the oracle's source with one plausible mistake fails the pin above
+    import os, subprocess
+    src = open(os.path.join(os.path.dirname(orc.__file__), "wfq_oracle.c")).read()
+    old, new = _QMR_PLANTS[plant]
+    assert src.count(old) == 1, plant
+    c = tmp_path / "planted.c"
+    c.write_text(src.replace(old, new))
+    so = tmp_path / "libplanted.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", str(c), "-o", str(so),
+                    "-lm"], check=True)
+    sysm, z, R, M = _qmr_system(orc, S)
+    assert _qmr_pin_deviation(sysm.operator(), sysm, z, R, M, library=orc.load(str(so))) > 1e-6
+
+
 def test_qmr_on_the_fly_equals_stored(orc, S):
     xyz = S.random_cluster(90, seed=17)
     p = _params(S, r0=2.7)
