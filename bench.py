@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--m", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="default cnt20k line: skip the other configurations' figures")
     ap.add_argument("--cpu-budget-s", type=float, default=25.0)
     ap.add_argument("--mode", default=None, choices=["solve", "apply", "serve", "spectrum"],
                     help="solve: block solves per second (default); apply: operator applies, "
@@ -68,6 +70,8 @@ def parse():
 # D storage per workload: FP64 + bf16 planes where both fit; bf16 planes only for the 150k
 # sphere (FP64 D would be 180 GB); nothing stored for the 1M-atom disk (matrix-free).
 def store_for(name, wfq, solver="gmres"):
+    if name == "sphere150k" and solver == "shifted":
+        return wfq.STORE_F32X2           # the FP32 pair planes alone: 180 GB
     if name == "sphere150k":
         # the symmetric FP32 pair tiles are 90 GB, the bf16 planes 90 GB: both fit
         return wfq.STORE_F32X2_SYM | wfq.STORE_BF16X2
@@ -79,6 +83,9 @@ def store_for(name, wfq, solver="gmres"):
 # DRAM bytes per stored D entry that ncu measured for one k_dgemv_df launch (cnt8k, N = 8200:
 # 549.5 MB read + written for 8200 x 8320 stored entries of the FP32 pair planes).
 DGEMV_DRAM_BYTES_PER_ENTRY = 549.5e6 / (8200.0 * 8320.0)
+
+# Algorithmic bytes of one block apply of D: the FP32 D (4 bytes per entry) read once.
+ALG_BYTES_PER_ENTRY = 4.0
 
 # FP32 lane-instructions per second of the whole GPU: 152 SMs x 128 lanes x 2070 MHz.
 FP32_LANE_OPS_PER_S = 152 * 128 * 2.07e9
@@ -402,16 +409,26 @@ def run_ours(args, rank, world, dist):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (one FP32 instruction per lane "
                                "per clock); work: 12 instructions per double-float multiply-add"}
     elif gv_n and gv_ms >= gemm_ms:
-        # shifted solver: the dominant kernel streams D (FP32 pair planes) once per launch
-        achieved_gbs = gv_bytes / (gv_ms * 1e-3) / 1e9
+        # shifted solver: the dominant kernel is the D product of the Arnoldi vectors.
+        # Algorithmic bytes per launch: 4 bytes per D entry (the FP32 D read once per block
+        # apply), N^2 entries.  The kernel itself stores D as FP32 pairs (8 bytes per entry
+        # for ~2^-48 products); its utilisation of HBM on those stored bytes is reported
+        # beside the fraction, under its own name.
+        avg_s = gv_ms / gv_n * 1e-3
+        alg_bytes = ALG_BYTES_PER_ENTRY * float(n) * float(n)
+        achieved_gbs = alg_bytes / avg_s / 1e9
         peak = peaks["hbm_gbs"]
+        stored = gv_bytes / gv_n
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                 "frac": achieved_gbs / peak,
                 "traffic": DGEMV_DRAM_BYTES_PER_ENTRY * n * (-(-n // 128) * 128),
                 "traffic_source": "ncu dram__bytes_read+write of k_dgemv_df at N = 8200 "
                                   "(the committed profile summary of that kernel), scaled per D entry to this N",
                 "kernel": "k_dgemv_df (double-float D product of the real Arnoldi vectors)", "launches": gv_n,
-                "avg_ms": gv_ms / gv_n, "bytes_per_launch": gv_bytes / gv_n,
+                "avg_ms": gv_ms / gv_n, "algorithmic_bytes_per_launch": alg_bytes,
+                "algorithmic_bytes_rule": "4 bytes per D entry x N^2 entries (FP32 D streamed once per block apply)",
+                "stored_bytes_per_launch": stored,
+                "hbm_util_of_stored_bytes": stored / avg_s / 1e9 / peak,
                 "peak_source": peak_src + " hbm_gbs (STREAM-style copy)"}
     elif gemm_n:
         gemm_avg_ms = gemm_ms / gemm_n
@@ -541,8 +558,61 @@ def run_ours(args, rank, world, dist):
         out["accuracy"]["alpha_columns_checked"] = sorted(alphas)
     g.close()
     ctx.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    if (mode == "solve" and args.workload == "cnt20k" and world == 1 and rank == 0
+            and not args.no_other_configs):
+        del q
+        torch.cuda.empty_cache()
+        out["other_configs"] = run_other_configs(args)
+    return out
+
+
+def _summary(o):
+    """The figures of a sub-run's JSON line that the default line carries."""
+    keep = {"metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "accuracy", "latency",
+            "cpu_baseline", "gpu_launches"}
+    out = {k: v for k, v in o.items() if k in keep}
+    cfg = o.get("config", {})
+    out["config"] = {k: cfg[k] for k in ("workload", "n_atoms", "columns", "requests", "solver", "path",
+                                         "arrival_rate_req_per_s") if k in cfg}
+    if o.get("roofline"):
+        out["roofline"] = {k: v for k, v in o["roofline"].items()
+                           if k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "avg_ms",
+                                    "hbm_util_of_stored_bytes", "peak_source")}
+    if "plain_fp64_gmres_same_gpu" in o:
+        pl = o["plain_fp64_gmres_same_gpu"]
+        out["plain_fp64_gmres_same_gpu"] = {"value": pl["value"], "unit": pl["unit"],
+                                            "served_over_plain": pl["served_over_plain"]}
+    if o.get("clocks"):
+        out["clocks"] = {k: o["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    return out
+
+
+def run_other_configs(args):
+    """The other configurations' figures, carried by the default cnt20k line: the 1M-atom
+    disk's matrix-free mixed apply (Gint/s against the derived ALU roof, sampled oracle
+    rows), a shortened serving stream (p50/p99 latency; served over plain per-column FP64
+    GMRES on the same GPU) and one shifted-GMRES step of the 150k-atom sphere (FP32 pair
+    planes).  Each runs in its own context after the cnt20k geometry is freed."""
+    import torch
+    plans = [
+        ("disk1m_apply", dict(workload="disk1m", mode="apply", steps=2, warmup=1, no_e2e=True)),
+        ("serve_240_requests", dict(workload="serve", mode="serve", requests=240, warmup=1)),
+        ("sphere150k_shifted", dict(workload="sphere150k", mode="solve", solver="shifted", steps=1, warmup=1,
+                                    no_e2e=True, no_other_solvers=True, no_other_configs=True)),
+    ]
+    res = {}
+    for key, kw in plans:
+        sub = argparse.Namespace(**vars(args))
+        sub.__dict__.update(kw)
+        t0 = time.perf_counter()
+        try:
+            res[key] = _summary(run_ours(sub, 0, 1, None))
+        except Exception as e:     # one failing configuration does not lose the headline line
+            res[key] = {"error": repr(e)[:400]}
+        res[key]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_bem(args, rank, world, dist):
@@ -661,8 +731,7 @@ def run_bem(args, rank, world, dist):
         out["accuracy"]["alpha_columns_checked"] = sorted(alphas)
     g.close()
     ctx.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 def run_apply(args, rank, world, dist, ctx, g, wl, store):
@@ -765,8 +834,7 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
                       "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
     g.close()
     ctx.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 # ------------------------------------------------------------------ serving
@@ -953,14 +1021,10 @@ def run_serve(args, rank, world, dist):
     for gm in geoms:
         gm.close()
     ctx.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 # ------------------------------------------------------------------ spectrum
-
-C_AU = 137.035999   # speed of light, atomic units
-
 
 def run_spectrum(args, rank, world, dist):
     """A whole absorption spectrum in one shifted solve: the workload's structure on a
@@ -996,14 +1060,11 @@ def run_spectrum(args, rank, world, dist):
     for _ in range(args.steps):
         _, st, status = g.solve_gmres_shifted(om, dirs, rel_tol=1e-8, max_iter=4000, prec=prec, out=q,
                                               stream=stream)
-    alpha = g.polarizability(q, stream=stream)
+        sig, sig_iso = g.cross_section(om, dirs, q, stream=stream)    # Eq. 28 per column, Eq. 29
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
-    a3 = alpha.reshape(nf, 3, 3)                        # [f][field direction k][component k']
-    sig = np.stack([4.0 * np.pi * om / C_AU * a3[:, k, k].imag for k in range(3)], axis=1)
-    sig_iso = sig.mean(axis=1)
     ni = np.array([s["iters"] for s in st]).reshape(nf, 3)
     good = sum(1 for s in st if s["rel_residual"] <= 1e-8)
     ipk = int(np.argmax(sig_iso))
@@ -1025,8 +1086,7 @@ def run_spectrum(args, rank, world, dist):
            "clocks": clk}
     g.close()
     ctx.close()
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 def main():
@@ -1046,7 +1106,9 @@ def main():
         if args.impl == "reference":
             run_reference(args, rank, world)
         else:
-            run_ours(args, rank, world, dist)
+            out = run_ours(args, rank, world, dist)
+            if rank == 0 and out is not None:
+                print(json.dumps(out), flush=True)
     finally:
         if dist is not None:
             dist.destroy_process_group()

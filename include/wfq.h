@@ -147,6 +147,13 @@ const char *wfq_last_error(void);
  * Profiling aid: the difference across a region counts the library's launches in it. */
 int64_t wfq_kernel_launches(void);
 
+/* Device-memory accounting (a deployment aid; the paper has no counterpart).
+ * out[0]: device allocations the library has requested in this process so far (all
+ * contexts, all threads; pool and plain allocations); out[1]: bytes the context's
+ * stream-ordered pool holds reserved; out[2]: bytes of it in use now; out[3]: the
+ * pool's in-use high-water mark.  out: host, 4 values, caller-owned. */
+int wfq_memory_stats(wfq_ctx *ctx, int64_t *out);
+
 /* Kernel timing (profiling aid).  While enabled, the library records a pair of CUDA
  * events on the launching stream around every launch of the kernels below;
  * wfq_profile_read synchronises those events and returns the launch count and the
@@ -246,13 +253,18 @@ int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, vo
  * budget or arena, or in a context where cudaMalloc is not allowed or would stall the
  * device -- and it computes exactly what wfq_apply(..., WFQ_PREC_MIXED, ...) computes
  * with the same kernels.
- *   - x, y: DEVICE pointers, N x ncplx complex64 atom-major (host pointers are
- *     rejected with WFQ_EINVAL, since staging them would allocate).  omega: host,
- *     ncplx values.  The caller still owns and passes all inputs and outputs.
+ *   - x, y: DEVICE pointers of the context's device, N x ncplx complex64 atom-major
+ *     (host pointers and other devices' pointers are rejected with WFQ_EINVAL, since
+ *     staging them would allocate).  omega: host, ncplx values, read during the call
+ *     and handed to the device as a kernel argument (no copy of the caller's array), so
+ *     ncplx <= 1024.  The caller still owns and passes all inputs and outputs.
  *   - Scratch (the bf16 planes of x, u = D x and the shifts) lives in one static
  *     32 MiB device array that every device which loads the library keeps until the
- *     process exits.  A call needing more -- about 4*ceil64(2*ncplx)*ceil128(N) +
- *     8*N*ncplx bytes -- fails with WFQ_EINVAL and a message; use wfq_apply then.
+ *     process exits.  A call needs
+ *         4*ceil32(2*ncplx)*ceil128(N) + align256(8*N*ncplx) + align256(16*ncplx)
+ *     bytes of it (ceilK: rounded up to a multiple of K; align256: to 256 bytes); a
+ *     call needing more than 32 MiB fails with WFQ_EINVAL and a message; use wfq_apply
+ *     then.
  *   - The first call on a device looks up the array's device address (once per
  *     device, with that device current); make that first call before any stream
  *     capture.
@@ -335,6 +347,22 @@ int wfq_solve_qmr(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
 int wfq_polarizability(wfq_geom *g, int64_t ncols, const double *q, double E0,
                        double *alpha, void *stream);
 
+/* Cross sections of solved columns (Section 4.1): the longitudinal cross section of
+ * Eq. 28, sigma_k(w) = (4 pi w / c) sum_i (k_i / E0) Im q_i^k, for each column
+ * c = f * ndir + d, with k = dirs[d] / |dirs[d]| and the field amplitude E0 |dirs[d]|
+ * (the field the solvers apply for that direction), i.e.
+ *     sigma[c] = (4 pi omega[f] / c) Im(dirs[d] . alpha_c) / |dirs[d]|^2,
+ * alpha_c of wfq_polarizability; and, when sigma_iso is not NULL, the mean over the
+ * ndir directions per frequency -- the isotropic cross section of Eq. 29 when the
+ * directions are x, y, z (any orthonormal triad).  c = 137.035999084 (atomic units).
+ *   omega: host, nfreq values (hartree); dirs: host, ndir x 3 (non-zero, finite).
+ *   q: N x (nfreq * ndir) complex128, host or device (the solvers' output layout).
+ *   sigma: nfreq x ndir FP64 (bohr^2), sigma_iso: nfreq FP64 or NULL; host or device.
+ * Blocks until the results are written.  WFQ_EINVAL on NULL, empty, non-finite or
+ * zero-length arguments. */
+int wfq_cross_section(wfq_geom *g, int64_t nfreq, const double *omega, int ndir, const double *dirs,
+                      double E0, const double *q, double *sigma, double *sigma_iso, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A request server on one context: `nworkers` threads, each with its own CUDA stream,
@@ -351,9 +379,11 @@ int wfq_polarizability(wfq_geom *g, int64_t ncols, const double *q, double E0,
  * WFQ_PREC_MIXED).  BEM geometries (wfq_build_bem_geometry, which always store the FP64
  * operator) take the shifted path; their continuations run in FP64 unless the bf16 planes
  * are stored too.
- *   budget_bytes: device memory the batches in flight may use together (Krylov bases,
- *   blocks, scratch; the geometries themselves are not counted).  A batch that alone
- *   exceeds it still runs when nothing else is in flight. */
+ *   budget_bytes: device memory for the structures in use plus the batches in flight:
+ *   a batch starts only while the device bytes of every geometry with requests queued or
+ *   running (wfq_geometry_info's device_bytes), the footprints of the batches in flight (Krylov
+ *   bases, blocks, scratch) and its own footprint fit in it; otherwise it waits until
+ *   running batches finish.  A batch still runs when nothing else is in flight. */
 typedef struct wfq_server wfq_server;
 int wfq_server_create(wfq_ctx *ctx, int nworkers, int64_t budget_bytes, int max_columns,
                       wfq_server **out);
@@ -361,7 +391,8 @@ int wfq_server_create(wfq_ctx *ctx, int nworkers, int64_t budget_bytes, int max_
 /* Queues one request: nfreq frequencies x ndir directions (columns c = f * ndir + d, as in
  * wfq_solve_gmres).  q_host (N x ncols complex128) and stats (ncols, or NULL) are host
  * buffers the caller keeps valid until the request is complete; the server writes them.
- * Returns at once with *request_id.  WFQ_ENOMEM if the request alone cannot fit the budget,
+ * Returns at once with *request_id.  WFQ_ENOMEM if the request's footprint plus its
+ * geometry's device bytes cannot fit the budget,
  * WFQ_ESINGULAR for omega = 0. */
 int wfq_server_submit(wfq_server *s, wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
                       const double *dirs, double E0, int m, double rel_tol, int max_iter,

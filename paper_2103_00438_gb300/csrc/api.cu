@@ -11,8 +11,10 @@ namespace wfq {
 
 static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<int64_t> g_allocs{0};   // device allocations requested by the library
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 const char *get_error() { return g_last_error.c_str(); }
@@ -20,6 +22,7 @@ const char *get_error() { return g_last_error.c_str(); }
 int dalloc(wfq_ctx *ctx, void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    note_alloc();
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -116,19 +119,22 @@ int check_device_error(wfq_ctx *ctx, cudaStream_t s) {
     return WFQ_OK;
 }
 
-bool is_device_ptr(const void *p) {
+int device_ptr_on(const void *p, int device) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return 1;
+    if (at.type != cudaMemoryTypeDevice) return 0;
+    return at.device == device ? 1 : -1;
 }
 
 // Synchronous device allocation owned by a geometry.
 template <class T>
 static int galloc(wfq_geom *g, T **p, size_t count) {
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    note_alloc();
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -175,7 +181,9 @@ struct Staged {
     DevBuf<T> buf;
     int in(wfq_ctx *ctx, const T *p, size_t cnt, bool copy, cudaStream_t s) {
         count = cnt;
-        if (is_device_ptr(p)) {
+        const int where = device_ptr_on(p, ctx->device);
+        if (where < 0) return fail(WFQ_EINVAL, "a device pointer argument lives on another device than the context's");
+        if (where > 0) {
             dev = const_cast<T *>(p);
             return WFQ_OK;
         }
@@ -221,6 +229,23 @@ const char *wfq_last_error(void) { return get_error(); }
 
 int64_t wfq_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int wfq_memory_stats(wfq_ctx *ctx, int64_t *out) {
+    if (!ctx || !out) return fail(WFQ_EINVAL, "NULL argument");
+    out[0] = g_allocs.load(std::memory_order_relaxed);
+    const cudaMemPoolAttr attrs[3] = {cudaMemPoolAttrReservedMemCurrent, cudaMemPoolAttrUsedMemCurrent,
+                                      cudaMemPoolAttrUsedMemHigh};
+    for (int k = 0; k < 3; ++k) {
+        unsigned long long v = 0;
+        cudaError_t e = cudaMemPoolGetAttribute(ctx->pool, attrs[k], &v);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(WFQ_ECUDA, std::string("cudaMemPoolGetAttribute: ") + cudaGetErrorString(e));
+        }
+        out[1 + k] = (int64_t)v;
+    }
+    return WFQ_OK;
+}
+
 int wfq_create(wfq_ctx **out, int device) {
     if (!out) return fail(WFQ_EINVAL, "ctx out-pointer is NULL");
     *out = nullptr;
@@ -247,6 +272,7 @@ int wfq_create(wfq_ctx **out, int device) {
     }
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    note_alloc();
     e = cudaMalloc(&ctx->dev_err, 256);
     if (e == cudaSuccess) e = cudaMemset(ctx->dev_err, 0, 256);
     if (e != cudaSuccess) {
@@ -475,6 +501,7 @@ int wfq_build_bem_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const dou
     }
     // device flag of the build kernel: two elements closer than 1e-8 bohr (freed below)
     int *close = nullptr;
+    note_alloc();
     cudaError_t e = cudaMalloc(&close, sizeof(int));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -666,6 +693,38 @@ int wfq_polarizability(wfq_geom *g, int64_t ncols, const double *q, double E0, d
     WFQ_TRY(A.in(g->ctx, reinterpret_cast<double2 *>(alpha), (size_t)ncols * 3, false, s));
     WFQ_TRY(launch_polarizability(g, ncols, Q.dev, E0, A.dev, s));
     WFQ_TRY(A.out(s));
+    WFQ_CUDA(cudaStreamSynchronize(s));
+    return WFQ_OK;
+}
+
+int wfq_cross_section(wfq_geom *g, int64_t nfreq, const double *omega, int ndir, const double *dirs,
+                      double E0, const double *q, double *sigma, double *sigma_iso, void *stream) {
+    if (!g || !omega || !dirs || !q || !sigma) return fail(WFQ_EINVAL, "NULL argument");
+    if (nfreq < 1 || ndir < 1) return fail(WFQ_EINVAL, "nfreq and ndir must be >= 1");
+    if (!std::isfinite(E0) || E0 == 0.0) return fail(WFQ_EINVAL, "E0 must be finite and non-zero");
+    for (int64_t f = 0; f < nfreq; ++f)
+        if (!std::isfinite(omega[f])) return fail(WFQ_EINVAL, "omega has a non-finite entry");
+    for (int d = 0; d < ndir; ++d) {
+        const double *k = dirs + 3 * d;
+        const double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        if (!(std::isfinite(kk) && kk > 0.0)) return fail(WFQ_EINVAL, "each direction must be finite and non-zero");
+    }
+    DeviceGuard dg(g->ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t ncols = nfreq * (int64_t)ndir;
+    Staged<double2> Q;
+    WFQ_TRY(Q.in(g->ctx, reinterpret_cast<const double2 *>(q), (size_t)g->n * ncols, true, s));
+    DevBuf<double> par;   // omega, then dirs
+    WFQ_TRY(par.alloc(g->ctx, (size_t)nfreq + 3 * (size_t)ndir, s));
+    WFQ_CUDA(cudaMemcpyAsync(par.ptr, omega, sizeof(double) * nfreq, cudaMemcpyHostToDevice, s));
+    WFQ_CUDA(cudaMemcpyAsync(par.ptr + nfreq, dirs, sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, s));
+    Staged<double> SG, SI;
+    WFQ_TRY(SG.in(g->ctx, sigma, (size_t)ncols, false, s));
+    if (sigma_iso) WFQ_TRY(SI.in(g->ctx, sigma_iso, (size_t)nfreq, false, s));
+    WFQ_TRY(launch_cross_section(g, nfreq, ndir, par.ptr, par.ptr + nfreq, Q.dev, E0, SG.dev,
+                                 sigma_iso ? SI.dev : nullptr, s));
+    WFQ_TRY(SG.out(s));
+    if (sigma_iso) WFQ_TRY(SI.out(s));
     WFQ_CUDA(cudaStreamSynchronize(s));
     return WFQ_OK;
 }

@@ -221,7 +221,9 @@ struct KScope {
 int check_device_error(wfq_ctx *ctx, cudaStream_t s);
 
 // True if p is a device (or managed) pointer usable by kernels.
-bool is_device_ptr(const void *p);
+// 1: device memory of `device` (or managed memory); 0: host memory; -1: device memory of
+// another device (kernels of this context must not touch it).
+int device_ptr_on(const void *p, int device);
 
 // ------------------------------------------------------------------ geometry build
 
@@ -234,6 +236,11 @@ int launch_build_d(const wfq_geom *g, cudaStream_t s);
 int launch_build_bem(const wfq_geom *g, int *close, cudaStream_t s);
 int launch_rhs(const wfq_geom *g, int ndir, const double *dirs_dev, double E0, double *R,
                cudaStream_t s);
+// sigma_{f,d} (Eq. 28) of the nfreq x ndir columns of q, and their per-frequency mean (Eq. 29)
+// when sigma_iso_dev is not null.  omega_dev, dirs_dev: device copies of the caller's arrays.
+int launch_cross_section(const wfq_geom *g, int64_t nfreq, int ndir, const double *omega_dev,
+                         const double *dirs_dev, const double2 *q, double E0, double *sigma_dev,
+                         double *sigma_iso_dev, cudaStream_t s);
 int launch_polarizability(const wfq_geom *g, int64_t ncols, const double2 *q, double E0,
                           double2 *alpha_dev, cudaStream_t s);
 

@@ -337,4 +337,42 @@ int launch_polarizability(const wfq_geom *g, int64_t ncols, const double2 *q, do
     return WFQ_OK;
 }
 
+// Eq. 28 and Eq. 29 from the polarizability of each column: with the field along
+// k = dir / |dir| at amplitude E0 |dir|, sum_i (r_i . k) Im q_i / (E0 |dir|) = Im(dir . alpha_c) / |dir|^2
+// (alpha_c = sum_i q_i r_i / E0), so sigma_{f,d} = (4 pi w_f / c) Im(dir_d . alpha_c) / |dir_d|^2.
+// One thread per frequency: its ndir columns and their mean (Eq. 29 for an orthonormal triad).
+__global__ void k_cross_section(int64_t nfreq, int ndir, const double *__restrict__ omega,
+                                const double *__restrict__ dirs, const double2 *__restrict__ alpha,
+                                double *__restrict__ sigma, double *__restrict__ sigma_iso) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfreq) return;
+    const double c_au = 137.035999084;   // speed of light in atomic units (CODATA 2018)
+    const double pref = 4.0 * 3.14159265358979323846 * omega[f] / c_au;
+    double mean = 0.0;
+    for (int d = 0; d < ndir; ++d) {
+        const double *k = dirs + 3 * d;
+        const double2 *a = alpha + (f * ndir + d) * 3;
+        const double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        const double im = k[0] * a[0].y + k[1] * a[1].y + k[2] * a[2].y;
+        const double s = pref * im / kk;
+        sigma[f * ndir + d] = s;
+        mean += s;
+    }
+    if (sigma_iso) sigma_iso[f] = mean / ndir;
+}
+
+int launch_cross_section(const wfq_geom *g, int64_t nfreq, int ndir, const double *omega_dev,
+                         const double *dirs_dev, const double2 *q, double E0, double *sigma_dev,
+                         double *sigma_iso_dev, cudaStream_t s) {
+    const int64_t ncols = nfreq * ndir;
+    DevBuf<double2> alpha;
+    WFQ_TRY(alpha.alloc(g->ctx, (size_t)ncols * 3, s));
+    WFQ_TRY(launch_polarizability(g, ncols, q, E0, alpha.ptr, s));
+    k_cross_section<<<(unsigned)((nfreq + 127) / 128), 128, 0, s>>>(nfreq, ndir, omega_dev, dirs_dev, alpha.ptr,
+                                                                     sigma_dev, sigma_iso_dev);
+    note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
+}
+
 }  // namespace wfq

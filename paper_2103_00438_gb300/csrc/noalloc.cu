@@ -3,7 +3,8 @@
 // for example code running inside a pre-sized memory arena or a host callback where
 // cudaMalloc is forbidden or would synchronise the device.  Its scratch (the bf16 hi/lo
 // planes of x, the product u = D x and the shifts z) lives in one static device array
-// instead of coming from the allocator.
+// instead of coming from the allocator, and the frequencies reach the device as a
+// kernel argument instead of a copy.
 #include <atomic>
 #include <cmath>
 #include <mutex>
@@ -40,14 +41,18 @@ static int noalloc_scratch(int device, void **out) {
     return WFQ_OK;
 }
 
-// z(omega) of Eq. 12 computed in place: the omega values copied into the slot are
-// replaced by (Re z, Im z).
-__global__ void k_noalloc_z(int64_t ncplx, double n0, double tau, double2 *__restrict__ zw) {
+// The column frequencies travel as a kernel argument (no host-to-device copy of a
+// caller's array); one thread per column writes z(omega_c) into the scratch slot, with
+// the shift of the geometry's operator (z_eval: Eq. 12 for omega-FQ).
+constexpr int64_t kNoAllocMaxCols = 1024;
+struct NoallocOmega {
+    double w[kNoAllocMaxCols];
+};
+
+__global__ void k_noalloc_z(int64_t ncplx, ShiftModel m, NoallocOmega om, double2 *__restrict__ z) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncplx) return;
-    double w = zw[c].x;
-    double f = -w / (2.0 * n0 * tau);
-    zw[c] = make_double2(f * w * tau, f);
+    z[c] = z_eval(m, om.w[c]);
 }
 
 static inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -60,6 +65,9 @@ extern "C" int wfq_apply_mixed_noalloc(wfq_geom *g, int64_t ncplx, const double 
                                        void *stream) {
     if (!g || !omega || !x || !y) return fail(WFQ_EINVAL, "NULL argument");
     if (ncplx < 1) return fail(WFQ_EINVAL, "ncplx must be >= 1");
+    if (ncplx > kNoAllocMaxCols)
+        return fail(WFQ_EINVAL, "wfq_apply_mixed_noalloc takes at most " + std::to_string(kNoAllocMaxCols) +
+                                    " columns per call (its frequencies travel as a kernel argument); use wfq_apply");
     if (!g->Dhi) return fail(WFQ_EUNSUPPORTED, "the mixed apply needs WFQ_STORE_BF16X2");
     if (g->op != OP_WFQ) return fail(WFQ_EUNSUPPORTED, "wfq_apply_mixed_noalloc takes omega-FQ geometries only");
     for (int64_t c = 0; c < ncplx; ++c)
@@ -79,8 +87,8 @@ extern "C" int wfq_apply_mixed_noalloc(wfq_geom *g, int64_t ncplx, const double 
     if (prev != g->ctx->device) WFQ_CUDA(cudaSetDevice(g->ctx->device));
     int rc = WFQ_OK;
     do {
-        if (!is_device_ptr(x) || !is_device_ptr(y)) {
-            rc = fail(WFQ_EINVAL, "wfq_apply_mixed_noalloc takes device pointers for x and y");
+        if (device_ptr_on(x, g->ctx->device) <= 0 || device_ptr_on(y, g->ctx->device) <= 0) {
+            rc = fail(WFQ_EINVAL, "wfq_apply_mixed_noalloc takes device pointers of the context's device for x and y");
             break;
         }
         void *base = nullptr;
@@ -90,16 +98,12 @@ extern "C" int wfq_apply_mixed_noalloc(wfq_geom *g, int64_t ncplx, const double 
         float2 *u = reinterpret_cast<float2 *>(b + z_bytes);
         void *planes = b + z_bytes + u_bytes;
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-        // omega -> slot (strided into the .x of each double2), then z in place
-        cudaError_t e = cudaMemcpy2DAsync(z, sizeof(double2), omega, sizeof(double), sizeof(double), (size_t)ncplx,
-                                          cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) {
-            rc = fail(WFQ_ECUDA, std::string("omega upload: ") + cudaGetErrorString(e));
-            break;
-        }
-        k_noalloc_z<<<(unsigned)((ncplx + 127) / 128), 128, 0, s>>>(ncplx, g->p.n0, g->p.tau, z);
+        NoallocOmega om;
+        for (int64_t c = 0; c < ncplx; ++c) om.w[c] = omega[c];
+        k_noalloc_z<<<(unsigned)((ncplx + 127) / 128), 128, 0, s>>>(ncplx, shift_model(g), om, z);
         note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
             rc = fail(WFQ_ECUDA, std::string("z kernel: ") + cudaGetErrorString(e));
             break;
         }

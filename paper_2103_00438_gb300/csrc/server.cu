@@ -3,8 +3,9 @@
 //
 //   - Structures stay resident: requests reference geometries built once with
 //     wfq_build_geometry (D, Kbar, atom data stay on the device between requests).
-//   - Admission by device-memory footprint: a batch starts only while the footprints of
-//     the batches in flight plus its own stay within the server's budget.
+//   - Admission by device-memory footprint: a batch starts only while the device bytes of
+//     the structures with requests queued or running, the footprints of the batches in
+//     flight and its own footprint stay within the server's budget.
 //   - Continuous batching: when a worker becomes free it takes the oldest admissible
 //     request and merges into the same block solve every queued request on the same
 //     structure with the same solver settings (the columns of all of them share D and
@@ -95,7 +96,9 @@ __global__ void k_take_cols(uint32_t total, uint32_t nc, int64_t ncol, int64_t c
 struct wfq_server {
     wfq_ctx *ctx = nullptr;
     size_t budget = 0;
-    size_t in_use = 0;
+    size_t in_use = 0;      // footprints of the batches in flight
+    size_t resident = 0;    // device bytes of the structures with requests queued or running
+    std::unordered_map<const wfq_geom *, int64_t> refs;   // requests queued or running per structure
     int64_t max_cols = 384;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -106,6 +109,19 @@ struct wfq_server {
     bool stop = false;
     int64_t next_id = 1;
     int64_t batches = 0, merged = 0;
+
+    // Structure accounting (under the lock): a structure's bytes count against the budget
+    // while it has requests queued or running.
+    void hold(const wfq_geom *g) {
+        if (refs[g]++ == 0) resident += g->bytes;
+    }
+    void release(const wfq_geom *g) {
+        auto it = refs.find(g);
+        if (it != refs.end() && --it->second == 0) {
+            resident -= g->bytes;
+            refs.erase(it);
+        }
+    }
 
     // Pops a batch (under the lock).  Returns false when the server is stopping and the
     // queue is empty.
@@ -133,7 +149,7 @@ struct wfq_server {
                 } else {
                     need = wfq::solve_footprint(head->g, cols, head->m, WFQ_PREC_MIXED);
                 }
-                if (in_use == 0 || in_use + need <= budget) {
+                if (in_use == 0 || in_use + need + resident <= budget) {
                     batch.clear();
                     for (size_t k = pick.size(); k-- > 0;) {
                         batch.insert(batch.begin(), queue[pick[k]]);
@@ -171,6 +187,7 @@ struct wfq_server {
                 for (Request *r : batch) {
                     r->t_done = t1;
                     r->done = true;
+                    release(r->g);
                 }
             }
             cv_done.notify_all();
@@ -312,8 +329,9 @@ int wfq_server_submit(wfq_server *sv, wfq_geom *g, int64_t nfreq, const double *
     const int64_t cols = nfreq * ndir;
     if (cols > sv->max_cols) return fail(WFQ_EINVAL, "request has more columns than the server's batch limit");
     const size_t need = use_shifted(g) ? shifted_footprint(g, cols, ndir, 0) : solve_footprint(g, cols, m, WFQ_PREC_MIXED);
-    if (need > sv->budget)
-        return fail(WFQ_ENOMEM, "request footprint exceeds the server's memory budget");
+    if (need + g->bytes > sv->budget)
+        return fail(WFQ_ENOMEM, "the structure's device bytes plus the request's footprint exceed the server's "
+                                "memory budget");
     auto *r = new Request;
     r->g = g;
     r->omega.assign(omega, omega + nfreq);
@@ -335,6 +353,7 @@ int wfq_server_submit(wfq_server *sv, wfq_geom *g, int64_t nfreq, const double *
         r->id = sv->next_id++;
         sv->reqs[r->id] = r;
         sv->queue.push_back(r);
+        sv->hold(g);
         *request_id = r->id;
     }
     sv->cv_work.notify_one();

@@ -24,7 +24,8 @@ EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches",
            "wfq_build_bem_geometry", "wfq_free_geometry",
            "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_gmres_shifted", "wfq_solve_qmr",
            "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc",
-           "wfq_server_create", "wfq_server_submit", "wfq_server_poll", "wfq_server_destroy"]
+           "wfq_server_create", "wfq_server_submit", "wfq_server_poll", "wfq_server_destroy",
+           "wfq_memory_stats", "wfq_cross_section"]
 KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE, KT_ORTHO, KT_RESIDUAL, KT_DGEMV_DF = 0, 1, 2, 3, 4, 5
 
 
@@ -91,6 +92,8 @@ def load(path: str | None = None):
                                   ctypes.POINTER(D), ctypes.POINTER(INT)]
     L.wfq_server_destroy.argtypes = [_P]
     L.wfq_profile.argtypes = [_P, INT]
+    L.wfq_memory_stats.argtypes = [_P, _P]
+    L.wfq_cross_section.argtypes = [_P, I64, _P, INT, _P, D, _P, _P, _P, _P]
     L.wfq_profile_read.argtypes = [_P, INT, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
     for name in EXPORTS:
         if name not in ("wfq_last_error", "wfq_kernel_launches"):
@@ -175,6 +178,13 @@ class Context:
         n, ms, wk = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
         _check(_lib.wfq_profile_read(self.h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(wk)))
         return n.value, ms.value, wk.value
+
+    def memory_stats(self):
+        """{allocs, pool_reserved, pool_used, pool_used_high}: device allocations the library
+        has requested so far (process-wide) and the context pool's byte counts."""
+        out = np.zeros(4, dtype=np.int64)
+        _check(_lib.wfq_memory_stats(self.h, out.ctypes.data))
+        return dict(zip(("allocs", "pool_reserved", "pool_used", "pool_used_high"), (int(v) for v in out)))
 
     def close(self):
         if self.h:
@@ -297,6 +307,20 @@ class Geometry:
         out = np.empty((ncols, 3), dtype=np.complex128)
         _check(_lib.wfq_polarizability(self.h, ncols, pq, float(E0), _ptr(out), _stream_handle(stream)))
         return out
+
+    def cross_section(self, omega, dirs, q, E0=1.0, stream=None):
+        """(sigma (nfreq, ndir), sigma_iso (nfreq,)) from q (n, nfreq * ndir) complex128
+        solved for these frequencies and directions (Eq. 28 per column; Eq. 29's mean over
+        the directions)."""
+        om = _host_f64(np.atleast_1d(omega))
+        dirs = _host_f64(np.atleast_2d(dirs))
+        nf, nd = len(om), len(dirs)
+        q, pq = _buf(q, np.complex128, self.n, self.n * nf * nd, False, "q")
+        sig = np.empty((nf, nd), dtype=np.float64)
+        iso = np.empty(nf, dtype=np.float64)
+        _check(_lib.wfq_cross_section(self.h, nf, om.ctypes.data, nd, dirs.ctypes.data, float(E0), pq,
+                                      sig.ctypes.data, iso.ctypes.data, _stream_handle(stream)))
+        return sig, iso
 
 
 
