@@ -61,8 +61,14 @@ def parse():
                     help="solve: block solves per second (default); apply: operator applies, "
                          "pair interactions per second (default for disk1m); serve: seeded Poisson "
                          "request stream through the request server (default for workload serve)")
+    ap.add_argument("--fmm-order", type=int, default=0,
+                    help="D product by the fast multipole method of this order (0: direct): the apply "
+                         "mode's product, or the mixed inner products of a matrix-free solve")
     ap.add_argument("--requests", type=int, default=2000, help="serve mode: requests in the stream")
     ap.add_argument("--workers", type=int, default=3, help="serve mode: server worker streams")
+    ap.add_argument("--pool", default="small", choices=["small", "full"],
+                    help="serve mode: resident structures of 1k-20k atoms, or also the 50k flake, the 80k "
+                         "tube and the 100k sphere")
     ap.add_argument("--load", type=float, default=0.8, help="serve mode: arrival rate / measured capacity")
     return ap.parse_args()
 
@@ -329,6 +335,8 @@ def run_ours(args, rank, world, dist):
     store = store_for(args.workload, wfq, args.solver)
     g = wfq.Geometry(ctx, xyz, p, store=store)
     mode = args.mode or ("apply" if args.workload in ("disk1m", "disk100k") else "solve")
+    if args.fmm_order and mode == "solve":
+        g.fmm_build(args.fmm_order)     # the mixed inner products of a matrix-free geometry
     if mode == "apply":
         return run_apply(args, rank, world, dist, ctx, g, wl, store)
     stream = torch.cuda.current_stream()
@@ -536,6 +544,24 @@ def run_ours(args, rank, world, dist):
         nbr = g.info()["nnz"] / n
         pairs_per_s = len(rows) * (2.0 + nbr) * n / secs
         mean_it = float(np.mean(iters))
+        # residual audit by the oracle on sampled rows: r_i = R_i - ((A - zI) q)_i, each
+        # row's neighbours and D entries recomputed by brute force (Eq. 13, Eq. 3, Eq. 17)
+        from oracle import oracle as orc
+        qh = q.cpu().numpy()
+        rng_a = np.random.default_rng(20210307)
+        audit_rows = np.sort(rng_a.choice(n, size=48, replace=False))
+        audits = []
+        for c in sorted({0, ncols - 1}):
+            f, d = divmod(c, nd)
+            Rr = orc.rhs_rows(xyz, p, dirs[d], audit_rows)
+            yr, _ = orc.apply_rows(xyz, p, orc.z_of_omega(om[f], p), qh[:, c], audit_rows)
+            Rfull = g.rhs(dirs[d:d + 1])[:, 0]
+            audits.append({"column": int(c), "sampled_rows": len(audit_rows),
+                           "rms_residual_over_rms_R_sampled": float(np.sqrt(np.mean(np.abs(Rr - yr) ** 2) /
+                                                                            np.mean(Rr ** 2))),
+                           "R_rows_vs_library": float(np.abs(Rr - Rfull[audit_rows]).max() / np.abs(Rfull).max()),
+                           "library_rel_residual": float(st_last[c]["rel_residual"])})
+        out["accuracy"]["oracle_residual_audit"] = audits
         out["cpu_baseline"] = {"value": pairs_per_s / (float(n) * n * mean_it), "unit": "solves/s",
                                "cores": os.cpu_count(), "kind": "oracle",
                                "sample": f"extrapolated: oracle row-sampled apply ({len(rows)} rows, D recomputed "
@@ -590,12 +616,13 @@ def _summary(o):
 def run_other_configs(args):
     """The other configurations' figures, carried by the default cnt20k line: the 1M-atom
     disk's matrix-free mixed apply (Gint/s against the derived ALU roof, sampled oracle
-    rows), a shortened serving stream (p50/p99 latency; served over plain per-column FP64
+    rows) and its fast-multipole apply (order 6), a shortened serving stream (p50/p99 latency; served over plain per-column FP64
     GMRES on the same GPU) and one shifted-GMRES step of the 150k-atom sphere (FP32 pair
     planes).  Each runs in its own context after the cnt20k geometry is freed."""
     import torch
     plans = [
         ("disk1m_apply", dict(workload="disk1m", mode="apply", steps=2, warmup=1, no_e2e=True)),
+        ("disk1m_fmm_apply", dict(workload="disk1m", mode="apply", fmm_order=6, steps=3, warmup=1, no_e2e=True)),
         ("serve_240_requests", dict(workload="serve", mode="serve", requests=240, warmup=1)),
         ("sphere150k_shifted", dict(workload="sphere150k", mode="solve", solver="shifted", steps=1, warmup=1,
                                     no_e2e=True, no_other_solvers=True, no_other_configs=True)),
@@ -749,8 +776,15 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
     x = torch.from_numpy(xh).cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
+    prec = wfq.PREC_MIXED
+    fmm_build_s = None
+    if args.fmm_order:
+        t0 = time.perf_counter()
+        g.fmm_build(args.fmm_order)
+        fmm_build_s = time.perf_counter() - t0
+        prec = wfq.PREC_FMM
     for _ in range(args.warmup):
-        g.apply(omc, x, y, prec=wfq.PREC_MIXED, stream=stream)
+        g.apply(omc, x, y, prec=prec, stream=stream)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -761,7 +795,7 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        g.apply(omc, x, y, prec=wfq.PREC_MIXED, stream=stream)
+        g.apply(omc, x, y, prec=prec, stream=stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -770,13 +804,18 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     gemm_n, gemm_ms, gemm_flops = ctx.profile_read(wfq.KT_GEMM_MIXED)
+    fmm_n, fmm_ms, _ = ctx.profile_read(wfq.KT_FMM)
     ctx.profile(False)
     ms = max_over_ranks(ms, dist)
     pairs = float(n) * float(n)
     value = pairs * args.steps * world / (ms * 1e-3) / 1e9
     peaks, peak_src = load_peaks()
     gemm_avg = gemm_ms / max(gemm_n, 1)
-    if store & wfq.STORE_BF16X2:
+    if args.fmm_order:
+        roof = {"bound": "fmm", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                "kernel": "fmm passes (p2m, m2m, m2l, l2l, l2p + near field)", "avg_ms": fmm_ms / max(fmm_n, 1),
+                "tree": g.fmm_info(), "build_s": fmm_build_s}
+    elif store & wfq.STORE_BF16X2:
         ach = gemm_flops / (gemm_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -794,9 +833,10 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
                 "tensor_tflops": gemm_flops / (gemm_ms * 1e-3) / 1e12}
     out = {"metric": "T-pair Gint/s", "value": value, "unit": "Gint/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "bf16x3+f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f32 (fmm)" if args.fmm_order else "bf16x3+f32", "data": "synthetic",
            "config": {"workload": args.workload, "n_atoms": n, "columns": 2 * ncplx,
-                      "path": "stored bf16 D" if store & wfq.STORE_BF16X2 else "matrix-free",
+                      "path": (f"fast multipole, order {args.fmm_order}" if args.fmm_order else
+                               "stored bf16 D" if store & wfq.STORE_BF16X2 else "matrix-free"),
                       "precision": "mixed: 3xBF16 D products, FP32 accumulation",
                       "parallelism": f"replicas{world}",
                       "l2": "inputs larger than L2" if n * n * 4 > 129e6 or n * 64 > 129e6 else "small"},
@@ -819,7 +859,8 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
             g_info = g.info()
             nbr = g_info["nnz"] / n
             row_pairs = float(len(rows)) * (2.0 + nbr) * n
-            out["accuracy"] = {"sampled_rows": len(rows), "max_err_over_bound": ratio, "bound_tolerance": 4e-5}
+            out["accuracy"] = {"sampled_rows": len(rows), "max_err_over_bound": ratio,
+                               "bound_tolerance": 1e-6 if args.fmm_order else 4e-5}
             out["cpu_baseline"] = {"value": row_pairs / secs / 1e9, "unit": "Gint/s", "cores": os.cpu_count(),
                                    "kind": "oracle",
                                    "sample": f"{len(rows)} rows of (A - zI)x with D recomputed from Eq. 3 for each "
@@ -828,7 +869,7 @@ def run_apply(args, rank, world, dist, ctx, g, wl, store):
         yh2 = np.empty_like(xh)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            g.apply(omc, xh, yh2, prec=wfq.PREC_MIXED)
+            g.apply(omc, xh, yh2, prec=prec)
         te = time.perf_counter() - t0
         out["e2e"] = {"value": pairs * args.steps * world / te / 1e9, "unit": "Gint/s",
                       "h2d_bytes_per_step": int(xh.nbytes), "d2h_bytes_per_step": int(xh.nbytes)}
@@ -853,13 +894,17 @@ def run_serve(args, rank, world, dist):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    mix = S.serving_mix(args.requests)
+    mix = S.serving_mix(args.requests, pool_size=args.pool)
     pool, reqs, gaps = mix["pool"], mix["requests"], mix["gaps"]
     ctx = wfq.Context(local)
-    store = wfq.STORE_FP64 | wfq.STORE_BF16X2 | wfq.STORE_F32X2
-    geoms = [wfq.Geometry(ctx, p["xyz"], p["params"], store=store) for p in pool]
+    # structures up to 20k atoms keep every D storage; the larger ones the FP64 D alone (the
+    # shifted solver splits it into float pairs as it streams it; plain FP64 GMRES reads it)
+    store = lambda p: (wfq.STORE_FP64 | wfq.STORE_BF16X2 | wfq.STORE_F32X2) if len(p["xyz"]) <= 20040 \
+        else wfq.STORE_FP64
+    geoms = [wfq.Geometry(ctx, p["xyz"], p["params"], store=store(p)) for p in pool]
     m, tol, max_iter = args.m, 1e-8, 4000
-    sv = wfq.Server(ctx, nworkers=args.workers, budget_bytes=96 << 30, max_columns=384)
+    resident = sum(gm.info()["device_bytes"] for gm in geoms)
+    sv = wfq.Server(ctx, nworkers=args.workers, budget_bytes=resident + (64 << 30), max_columns=384)
     ncol = lambda r: len(r[1]) * len(r[2])
 
     def closed_loop(batch):
@@ -999,6 +1044,7 @@ def run_serve(args, rank, world, dist):
                       "capacity_closed_loop_solves_per_s": capacity, "workers": args.workers,
                       "solver": "shifted gmres per batch (stored D), continuations gmres(50)",
                       "rel_tol": tol, "parallelism": f"replicas{world}",
+                      "resident_bytes": resident, "budget_bytes": resident + (64 << 30),
                       "l2": "resident D planes of all structures (%.1f GB) larger than L2" %
                             (sum(4.0 * len(p["xyz"]) ** 2 for p in pool) / 1e9)},
            "latency": {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),

@@ -113,13 +113,19 @@ enum {
     WFQ_PREC_FP64 = 0,     /* FP64 operator, complex128 vectors */
     WFQ_PREC_MIXED = 1,    /* D.x from 3 bf16 products (hi.hi + hi.lo + lo.hi) with FP32
                               accumulation on the tensor cores, D from the stored bf16 planes
-                              or generated from the coordinates; complex64 vectors; solves
-                              add iterative refinement on top, whose true residual uses
-                              WFQ_PREC_DF (FP64 kernels when D64 is not stored) */
-    WFQ_PREC_DF = 2        /* wfq_apply only: complex128 vectors, D.x with FP64 operands split
+                              or generated from the coordinates -- or, without stored planes
+                              and after wfq_fmm_build, by the fast multipole method (as
+                              WFQ_PREC_FMM, up to 256 columns per product); complex64
+                              vectors; solves add iterative refinement on top, whose true
+                              residual uses WFQ_PREC_DF (FP64 kernels when D64 is not
+                              stored) */
+    WFQ_PREC_DF = 2,       /* wfq_apply only: complex128 vectors, D.x with FP64 operands split
                               into float pairs and double-float accumulation (~2^-48 relative
                               per product) on the FP32 pipes; needs WFQ_STORE_FP64 and more
                               than 4 columns, else identical to WFQ_PREC_FP64 */
+    WFQ_PREC_FMM = 3       /* wfq_apply only: complex64 vectors, D.x by the fast multipole
+                              method built with wfq_fmm_build (near field by Eq. 3, far field
+                              1/r by Chebyshev interpolation), FP32 arithmetic */
 };
 
 /* Per-solve statistics. */
@@ -167,7 +173,8 @@ enum {
     WFQ_KT_RESIDUAL = 4,     /* FP64 true residual of a cycle (gathers, product, norms) */
     WFQ_KT_DGEMV_DF = 5,     /* shifted GMRES: double-float D product of the real Arnoldi
                                 vectors (one launch per group of <= 4 directions) */
-    WFQ_KT_COUNT = 6
+    WFQ_KT_FMM = 6,          /* the fast-multipole D product (all its passes) */
+    WFQ_KT_COUNT = 7
 };
 
 /* enable != 0: reset the counters and start recording; enable == 0: stop. */
@@ -176,7 +183,8 @@ int wfq_profile(wfq_ctx *ctx, int enable);
 /* Launches, summed device milliseconds and summed work of kernel class `kind` (WFQ_KT_*).
  * Work: WFQ_KT_GEMM_MIXED -- tensor flops of the three bf16 products, 6 N^2 C per launch
  * (C = real columns of that launch); WFQ_KT_DAPPLY_FP64 -- 2 N^2 C flops; WFQ_KT_DGEMV_DF --
- * algorithmic bytes of D read, 8 N^2 (the entries; padding columns not counted); others 0.
+ * algorithmic bytes of D read, 8 N^2 (the entries; padding columns not counted); WFQ_KT_FMM
+ * -- N^2, the pair interactions the product stands for; others 0.
  * Any out-pointer may be NULL. */
 int wfq_profile_read(wfq_ctx *ctx, int kind, int64_t *launches, double *total_ms, double *work);
 
@@ -276,6 +284,29 @@ int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, vo
  *     or freed by this call. */
 int wfq_apply_mixed_noalloc(wfq_geom *g, int64_t ncplx, const double *omega, const void *x,
                             void *y, void *stream);
+
+/* Far-field-compressed D product (the fast multipole method the paper's conclusions name
+ * as the way past the O(N^2) matrix-vector product; the paper gives no FMM of its own):
+ * builds, for an omega-FQ geometry, the tree and operators that wfq_apply(...,
+ * WFQ_PREC_FMM, ...) uses.  The method is the Chebyshev-interpolation FMM of Fong and
+ * Darve: a uniform tree over the bounding cube (a quadtree over the bounding square when
+ * all atoms share one z), as deep as leaves of side >= 6 max_ij sqrt(w_i^2 + w_j^2) allow
+ * (so every far pair has erf(r / s_ij) = 1 in FP64 and D_ij = 1 / r_ij exactly, Eq. 3);
+ * pairs in the same or adjacent leaves by Eq. 3; all other pairs through `order`
+ * Chebyshev nodes per dimension per box (P2M, M2M, M2L over interaction lists, L2L,
+ * L2P).  The far field's relative error falls geometrically with order (about 1e-6 of
+ * sum_j |D_ij x_j| at order 6 on a flat flake).  order: 2..16 for a flat structure, 2..6
+ * for a 3D one.  wfq_apply with WFQ_PREC_FMM takes at most 256 complex columns per call.
+ * Host work O(N log N) plus
+ * the operator tables (order^(2 dim) floats per offset); device memory is counted in the
+ * geometry's bytes and freed with it; a second call replaces the first.  WFQ_EUNSUPPORTED
+ * for BEM geometries, WFQ_EINVAL for an order out of range. */
+int wfq_fmm_build(wfq_geom *g, int order);
+
+/* The tree of wfq_fmm_build: out[0] dimension (2: quadtree, 3: octree), out[1] depth,
+ * out[2] order, out[3] non-empty leaves, out[4] non-empty boxes of all levels, out[5]
+ * interaction-list entries, out[6] near-list entries.  WFQ_EUNSUPPORTED if not built. */
+int wfq_fmm_info(const wfq_geom *g, int64_t *out);
 
 /* Right-hand sides R (Eq. 13 with the potential of Eq. 2) for ndir field
  * directions.  dirs: host, ndir x 3 (need not be unit vectors; the field is E0 * dir).

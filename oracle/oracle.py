@@ -65,6 +65,7 @@ def load(path):
     L.orc_residual_norm.restype = _D
     L.orc_vdot.argtypes = [_I64, _P, _P, _P]
     L.orc_apply_rows.argtypes = [_I64, _P, _P, _D, _D, _D, _D, _D, _D, _D, _P, _I64, _P, _P, _P]
+    L.orc_rhs_rows.argtypes = [_I64, _P, _D, _D, _D, _D, _D, _P, _D, _I64, _P, _P]
     return L
 
 
@@ -297,6 +298,17 @@ def apply_rows(xyz, p, z, x, rows, eta=None):
     lib().orc_apply_rows(n, _ptr(xyz), _ptr(eta), p["r0"], p["d_fermi"], p["s_fermi"], p["area"],
                          p["cutoff_eps"], z.real, z.imag, _ptr(x), len(rows), _ptr(rows), _ptr(y), _ptr(bound))
     return y, bound
+
+
+def rhs_rows(xyz, p, kdir, rows, E0=1.0):
+    """Selected rows of R (Eq. 13, Eq. 2), each row's neighbours by a brute-force scan."""
+    xyz = _f64(xyz)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    kd = _f64(np.asarray(kdir, dtype=np.float64))
+    out = np.empty(len(rows))
+    lib().orc_rhs_rows(len(xyz), _ptr(xyz), p["r0"], p["d_fermi"], p["s_fermi"], p["area"], p["cutoff_eps"],
+                       _ptr(kd), float(E0), len(rows), _ptr(rows), _ptr(out))
+    return out
 
 
 def vdot(u, v):

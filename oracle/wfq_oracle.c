@@ -640,6 +640,30 @@ void orc_apply_rows(int64_t n, const double *xyz, const double *eta, double r0, 
     }
 }
 
+/* Selected rows of R (Eq. 13 with the potential of Eq. 2), each row's neighbours found by a
+ * brute-force scan with the keep rule of orc_kbar_csr: R_i = sum_j Kbar_ij (V_i - V_j),
+ * V = -E0 (r . kdir).  For residual audits of structures too large for a CSR of Kbar. */
+void orc_rhs_rows(int64_t n, const double *xyz, double r0, double d_fermi, double s_fermi, double area,
+                  double cutoff_eps, const double *kdir, double E0, int64_t nrows, const int64_t *rows,
+                  double *R)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < nrows; ++t) {
+        int64_t i = rows[t];
+        double Vi = -E0 * (xyz[3 * i] * kdir[0] + xyz[3 * i + 1] * kdir[1] + xyz[3 * i + 2] * kdir[2]);
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r = dist(xyz, i, j);
+            double omf = 1.0 / (1.0 + exp(d_fermi * (r / (s_fermi * r0) - 1.0)));
+            if (omf < cutoff_eps) continue;
+            double Vj = -E0 * (xyz[3 * j] * kdir[0] + xyz[3 * j + 1] * kdir[1] + xyz[3 * j + 2] * kdir[2]);
+            s += (Vi - Vj) * (omf * area / r);
+        }
+        R[t] = s;
+    }
+}
+
 /* Complex Euclidean inner product, exported for tests of the Arnoldi basis. */
 void orc_vdot(int64_t n, const double *u, const double *v, double *out)
 {

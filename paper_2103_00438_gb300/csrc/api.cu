@@ -152,6 +152,7 @@ static void free_geom(wfq_geom *g) {
                     g->Dsym, g->sym_items, g->sym_item_start, g->elem};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    fmm_free(g->fmm);
     delete g;
 }
 
@@ -545,8 +546,12 @@ int wfq_geometry_info(const wfq_geom *g, int64_t *n, int64_t *nnz, int64_t *devi
 int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, void *y, int prec, void *stream) {
     if (!g || !omega || !x || !y) return fail(WFQ_EINVAL, "NULL argument");
     if (ncplx < 1) return fail(WFQ_EINVAL, "ncplx must be >= 1");
-    if (prec != WFQ_PREC_FP64 && prec != WFQ_PREC_MIXED && prec != WFQ_PREC_DF)
+    if (prec != WFQ_PREC_FP64 && prec != WFQ_PREC_MIXED && prec != WFQ_PREC_DF && prec != WFQ_PREC_FMM)
         return fail(WFQ_EINVAL, "unknown precision");
+    if (prec == WFQ_PREC_FMM && !g->fmm)
+        return fail(WFQ_EUNSUPPORTED, "WFQ_PREC_FMM needs wfq_fmm_build on this geometry first");
+    if (prec == WFQ_PREC_FMM && ncplx > 256)
+        return fail(WFQ_EINVAL, "WFQ_PREC_FMM applies at most 256 complex columns per call");
     if (!finite_all(omega, ncplx)) return fail(WFQ_EINVAL, "omega has a non-finite entry");
     DeviceGuard dg(g->ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -582,12 +587,40 @@ int wfq_apply(wfq_geom *g, int64_t ncplx, const double *omega, const void *x, vo
         DevBuf<float2> U;
         DevBuf<unsigned char> scratch;
         WFQ_TRY(U.alloc(g->ctx, nc, s));
-        WFQ_TRY(scratch.alloc(g->ctx, mixed_scratch_bytes(g, ncplx), s));
-        WFQ_TRY(d_apply_mixed(g, ncplx, X.dev, U.ptr, scratch.ptr, s));
+        if (prec == WFQ_PREC_FMM) {
+            WFQ_TRY(d_apply_fmm(g, ncplx, X.dev, U.ptr, s));
+        } else {
+            WFQ_TRY(scratch.alloc(g->ctx, mixed_scratch_bytes(g, ncplx), s));
+            WFQ_TRY(d_apply_mixed(g, ncplx, X.dev, U.ptr, scratch.ptr, s));
+        }
         WFQ_TRY(sparse_shift_fp32(g, ncplx, U.ptr, X.dev, z.ptr, Y.dev, s));
         WFQ_TRY(Y.out(s));
     }
     WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
+}
+
+int wfq_fmm_build(wfq_geom *g, int order) {
+    if (!g) return fail(WFQ_EINVAL, "geometry is NULL");
+    if (order < 2 || order > 16) return fail(WFQ_EINVAL, "FMM order must be in 2..16");
+    if (g->op != OP_WFQ) return fail(WFQ_EUNSUPPORTED, "the FMM product takes omega-FQ geometries only");
+    DeviceGuard dg(g->ctx->device);
+    WFQ_CUDA(cudaDeviceSynchronize());
+    Fmm *f = nullptr;
+    WFQ_TRY(fmm_build(g, order, &f));
+    if (g->fmm) {
+        g->bytes -= fmm_bytes(g->fmm);
+        fmm_free(g->fmm);
+    }
+    g->fmm = f;
+    g->bytes += fmm_bytes(f);
+    return WFQ_OK;
+}
+
+int wfq_fmm_info(const wfq_geom *g, int64_t *out) {
+    if (!g || !out) return fail(WFQ_EINVAL, "NULL argument");
+    if (!g->fmm) return fail(WFQ_EUNSUPPORTED, "wfq_fmm_build has not been called on this geometry");
+    fmm_info(g->fmm, out);
     return WFQ_OK;
 }
 

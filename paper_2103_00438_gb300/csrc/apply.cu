@@ -718,6 +718,9 @@ size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc) {
 
 int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
                   cudaStream_t s) {
+    // without stored planes, the fast-multipole product when its tree is built (at large N
+    // both faster and, at order >= 6, closer to D than the generated 3xBF16 tiles)
+    if (!g->Dhi && g->fmm && cc <= 256) return d_apply_fmm(g, cc, X, U, s);
     if (!g->Dhi) WFQ_TRY(require_wfq(g));
     const int64_t C = 2 * cc, cpad = mixed_cpad(cc), npad = g->npad;
     __nv_bfloat16 *xhi = reinterpret_cast<__nv_bfloat16 *>(scratch);

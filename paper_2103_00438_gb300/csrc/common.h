@@ -139,6 +139,10 @@ struct wfq_ctx {
     std::map<int64_t, int> tuned;
 };
 
+namespace wfq {
+struct Fmm;   // fast-multipole tree and operators (fmm.cu)
+}
+
 struct wfq_geom {
     wfq_ctx *ctx = nullptr;
     int op = wfq::OP_WFQ;   // operator family (wfq::OpKind)
@@ -177,6 +181,7 @@ struct wfq_geom {
     wfq::SymItem *sym_items = nullptr;   // work items of the symmetric product (device)
     int64_t sym_nitems = 0;
     int *sym_item_start = nullptr;       // [sym_nt + 1]: first item of each tile row (device)
+    wfq::Fmm *fmm = nullptr;             // wfq_fmm_build: tree and operators of the FMM product
 };
 
 namespace wfq {
@@ -261,6 +266,14 @@ int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cuda
 size_t mixed_scratch_bytes(const wfq_geom *g, int64_t cc);
 int d_apply_mixed(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, void *scratch,
                   cudaStream_t s);
+
+// Fast-multipole D product (fmm.cu): build the tree and operators of an order, free them,
+// their device bytes, the tree summary of wfq_fmm_info, and U = D X with it (FP32).
+int fmm_build(wfq_geom *g, int order, Fmm **out);
+void fmm_free(Fmm *f);
+size_t fmm_bytes(const Fmm *f);
+void fmm_info(const Fmm *f, int64_t *out);
+int d_apply_fmm(const wfq_geom *g, int64_t cc, const float2 *X, float2 *U, cudaStream_t s);
 
 // Y = Kbar U - P U - z_c X   (z: device, cc values); BEM geometries: Y = U - z_c X
 int sparse_shift_fp64(const wfq_geom *g, int64_t cc, const double2 *U, const double2 *X,

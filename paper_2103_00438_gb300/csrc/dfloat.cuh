@@ -29,6 +29,23 @@ __device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, f
     sl += t + e;
 }
 
+// The same multiply-add on two independent lanes at once with the packed FP32x2
+// instructions (one instruction per pair of FP32 operations: half the issue slots of
+// df_mac, the same arithmetic on each lane).
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void df_mac2(float2 ah, float2 al, float2 bh, float2 bl, float2 &sh, float2 &sl) {
+    const float2 p = __fmul2_rn(ah, bh);
+    float2 e = __ffma2_rn(ah, bh, f2neg(p));          // exact rounding error of p
+    e = __ffma2_rn(ah, bl, e);
+    e = __ffma2_rn(al, bh, e);
+    const float2 s = __fadd2_rn(sh, p);
+    const float2 v = __fadd2_rn(s, f2neg(sh));
+    const float2 t = __fadd2_rn(__fadd2_rn(sh, f2neg(__fadd2_rn(s, f2neg(v)))), __fadd2_rn(p, f2neg(v)));
+    sh = s;
+    sl = __fadd2_rn(sl, __fadd2_rn(t, e));
+}
+
 // (sh, sl) += (bh, bl)
 __device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl) {
     const float s = __fadd_rn(sh, bh);

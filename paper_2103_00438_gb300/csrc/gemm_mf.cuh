@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
 // One launch for a group of <= 512 accumulator columns.
 inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad, const __nv_bfloat16 *Xhi,
                                    const __nv_bfloat16 *Xlo, int cpad, float *U, int64_t ldu, int64_t ncols,
-                                   int num_sms, int *err, cudaStream_t s, std::string *msg) {
+                                   int num_sms, int *err, cudaStream_t s, std::string *msg,
+                                   int stages_req = 0) {
     MfParams mp{};
     Params &p = mp.p;
     p.n = n;
@@ -353,6 +354,7 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
     p.stage_bytes = (2 * A_BYTES + 2 * p.b_bytes + MF_ATOM_BYTES + 1023) / 1024 * 1024;
     p.stages = (int)((kMaxDynSmem - 2048) / p.stage_bytes);
     if (p.stages > MAX_STAGES) p.stages = MAX_STAGES;
+    if (stages_req >= 2 && stages_req < p.stages) p.stages = stages_req;   // a shallower pipeline (autotuner)
     int tcols = 32;
     while (tcols < cpad) tcols <<= 1;
     p.tmem_cols = tcols;
@@ -379,7 +381,7 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
 
 inline cudaError_t gemm3_mf(const float4 *atoms, int64_t n, int64_t npad, const __nv_bfloat16 *Xhi,
                             const __nv_bfloat16 *Xlo, int64_t cpad, float *U, int64_t ldu, int num_sms, int *err,
-                            cudaStream_t s, int *launches, std::string *msg) {
+                            cudaStream_t s, int *launches, std::string *msg, int stages_req = 0) {
     if (npad % BM != 0 || cpad % 32 != 0 || cpad < ldu || ldu < 1) {
         if (msg) *msg = "gemm_mf: bad shape";
         return cudaErrorInvalidValue;
@@ -392,7 +394,7 @@ inline cudaError_t gemm3_mf(const float4 *atoms, int64_t n, int64_t npad, const 
         const int group = (int)((cpad - c0) < 512 ? (cpad - c0) : 512);
         const int64_t valid = (ldu - c0) < group ? (ldu - c0) : group;
         cudaError_t e = launch_group_mf(atoms, n, npad, Xhi + c0 * npad, Xlo + c0 * npad, group, U + c0, ldu, valid,
-                                        num_sms, err, s, msg);
+                                        num_sms, err, s, msg, stages_req);
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
     }

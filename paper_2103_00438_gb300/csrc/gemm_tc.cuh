@@ -432,7 +432,7 @@ inline int64_t grid_size(int64_t mtiles, int num_sms) {
 // *msg describes failures that are not CUDA runtime errors.
 inline cudaError_t launch_group(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *Dlo, int64_t n, int64_t npad,
                                 const __nv_bfloat16 *Xhi, const __nv_bfloat16 *Xlo, int cpad, float *U, int64_t ldu,
-                                int64_t ncols, int num_sms, int *err, cudaStream_t s, std::string *msg) {
+                                int64_t ncols, int num_sms, int *err, cudaStream_t s, std::string *msg, int stages_req = 0) {
     Params p{};
     p.n = n;
     p.ldu = ldu;
@@ -447,6 +447,7 @@ inline cudaError_t launch_group(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *D
     p.stage_bytes = 2 * A_BYTES + 2 * p.b_bytes;
     p.stages = (int)((kMaxDynSmem - 2048) / p.stage_bytes);
     if (p.stages > MAX_STAGES) p.stages = MAX_STAGES;
+    if (stages_req >= 2 && stages_req < p.stages) p.stages = stages_req;   // a shallower pipeline (autotuner)
     int tc = 32;
     while (tc < cpad) tc <<= 1;
     p.tmem_cols = tc;
@@ -475,7 +476,7 @@ inline cudaError_t launch_group(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *D
 // Full launch: accumulator columns in groups of at most 512.  U must not alias X.
 inline cudaError_t gemm3_tc(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *Dlo, int64_t n, int64_t npad,
                             const __nv_bfloat16 *Xhi, const __nv_bfloat16 *Xlo, int64_t cpad, float *U, int64_t ldu,
-                            int num_sms, int *err, cudaStream_t s, int *launches, std::string *msg) {
+                            int num_sms, int *err, cudaStream_t s, int *launches, std::string *msg, int stages_req = 0) {
     if (npad % BM != 0 || cpad % 32 != 0 || cpad < ldu || ldu < 1) {
         if (msg) *msg = "gemm_tc: bad shape";
         return cudaErrorInvalidValue;
@@ -489,7 +490,7 @@ inline cudaError_t gemm3_tc(const __nv_bfloat16 *Dhi, const __nv_bfloat16 *Dlo, 
         const int group = (int)((cpad - c0) < 512 ? (cpad - c0) : 512);
         const int64_t valid = (ldu - c0) < group ? (ldu - c0) : group;
         cudaError_t e = launch_group(Dhi, Dlo, n, npad, Xhi + c0 * npad, Xlo + c0 * npad, group, U + c0, ldu, valid,
-                                     num_sms, err, s, msg);
+                                     num_sms, err, s, msg, stages_req);
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;
     }

@@ -97,11 +97,12 @@ __global__ void __launch_bounds__(GV_WARPS * 32, MINB) k_dgemv_df(int64_t n, int
             rowh[r] = rowl[r] = nullptr;
         }
     }
-    float sh[ROWS][C], sl[ROWS][C];
+    // accumulators per (row, vector): even and odd columns in the two lanes of a float2
+    float2 sh2[ROWS][C], sl2[ROWS][C];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r)
 #pragma unroll
-        for (int d = 0; d < C; ++d) sh[r][d] = sl[r][d] = 0.f;
+        for (int d = 0; d < C; ++d) sh2[r][d] = sl2[r][d] = make_float2(0.f, 0.f);
 
     for (int64_t j0 = 0; j0 < n; j0 += GV_CHUNK) {
         __syncthreads();
@@ -152,16 +153,25 @@ __global__ void __launch_bounds__(GV_WARPS * 32, MINB) k_dgemv_df(int64_t n, int
                     const float4 xl4 = *reinterpret_cast<const float4 *>(&sxl[d][jl]);
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) {
-                        df_mac(dh[t][r].x, dl[t][r].x, xh4.x, xl4.x, sh[r][d], sl[r][d]);
-                        df_mac(dh[t][r].y, dl[t][r].y, xh4.y, xl4.y, sh[r][d], sl[r][d]);
-                        df_mac(dh[t][r].z, dl[t][r].z, xh4.z, xl4.z, sh[r][d], sl[r][d]);
-                        df_mac(dh[t][r].w, dl[t][r].w, xh4.w, xl4.w, sh[r][d], sl[r][d]);
+                        df_mac2(make_float2(dh[t][r].x, dh[t][r].y), make_float2(dl[t][r].x, dl[t][r].y),
+                                make_float2(xh4.x, xh4.y), make_float2(xl4.x, xl4.y), sh2[r][d], sl2[r][d]);
+                        df_mac2(make_float2(dh[t][r].z, dh[t][r].w), make_float2(dl[t][r].z, dl[t][r].w),
+                                make_float2(xh4.z, xh4.w), make_float2(xl4.z, xl4.w), sh2[r][d], sl2[r][d]);
                     }
                 }
             }
         }
     }
-    // warp sums in double-float, fixed butterfly order
+    // the two lanes, then warp sums in double-float, fixed butterfly order
+    float sh[ROWS][C], sl[ROWS][C];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int d = 0; d < C; ++d) {
+            sh[r][d] = sh2[r][d].x;
+            sl[r][d] = sl2[r][d].x;
+            df_add(sh[r][d], sl[r][d], sh2[r][d].y, sl2[r][d].y);
+        }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r)
 #pragma unroll
@@ -315,10 +325,10 @@ void launch_dgemv(int tiling, int64_t n, int64_t ld, const float *Fh, const floa
                   const float *xh, const float *xl, double *U, cudaStream_t s) {
     const unsigned b1 = (unsigned)((n + GV_WARPS - 1) / GV_WARPS), b2 = (unsigned)((n + 2 * GV_WARPS - 1) / (2 * GV_WARPS));
     switch (tiling) {
-        case 1: k_dgemv_df<C, PL, 2, 4, 3><<<b2, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
-        case 2: k_dgemv_df<C, PL, 2, 2, 4><<<b2, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
-        case 3: k_dgemv_df<C, PL, 1, 8, 3><<<b1, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
-        default: k_dgemv_df<C, PL, 1, 4, 4><<<b1, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+        case 1: k_dgemv_df<C, PL, 2, 4, 2><<<b2, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+        case 2: k_dgemv_df<C, PL, 2, 2, 3><<<b2, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+        case 3: k_dgemv_df<C, PL, 1, 8, 2><<<b1, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
+        default: k_dgemv_df<C, PL, 1, 4, 3><<<b1, GV_WARPS * 32, 0, s>>>(n, ld, Fh, Fl, D64, xh, xl, U); break;
     }
 }
 

@@ -316,11 +316,13 @@ def workload(name: str) -> dict:
     raise KeyError(name)
 
 
-def serving_mix(n_requests: int = 2000, seed: int = 20210305) -> dict:
+def serving_mix(n_requests: int = 2000, seed: int = 20210305, pool_size: str = "small") -> dict:
     """Seeded serving stream over a resident pool of structures from the paper's three
     families (honeycomb flakes, armchair (n, n) nanotubes, fcc sodium-like spheres).
 
-    pool      list of dicts: name, xyz (bohr), params, band (eV) -- 1k to 20k atoms
+    pool      list of dicts: name, xyz (bohr), params, band (eV) -- 1k to 20k atoms; with
+              pool_size="full" also the largest members of each family's range (a 50k-atom
+              flake, an 80k-atom (15,15) tube, a 100k-atom sphere)
     requests  list of (structure index, omega (hartree, sorted), dirs (ndir x 3)); each
               request draws its structure uniformly from the pool, 1-64 frequencies
               uniform in the family's band and 1-3 field directions (x, then y, then z)
@@ -339,6 +341,15 @@ def serving_mix(n_requests: int = 2000, seed: int = 20210305) -> dict:
         {"name": "sphere10k", "xyz": fcc_sphere(a_na, fcc_sphere_radius_for(10000, a_na), 0.05, seed=seed + 1),
          "params": sodium_params(), "band": (0.9, 1.8)},
     ]
+    if pool_size == "full":
+        pool += [
+            {"name": "flake50k", "xyz": honeycomb_flake(91), "params": carbon_params(1.51), "band": (0.05, 2.0)},
+            {"name": "cnt15_80k", "xyz": nanotube(15, 15, 1334), "params": carbon_params(1.04), "band": (0.05, 2.0)},
+            {"name": "sphere100k", "xyz": fcc_sphere(a_na, fcc_sphere_radius_for(100000, a_na), 0.05, seed=seed + 2),
+             "params": sodium_params(), "band": (0.9, 1.8)},
+        ]
+    elif pool_size != "small":
+        raise ValueError(pool_size)
     rng = np.random.default_rng(seed)
     dirs3 = np.eye(3)
     reqs = []

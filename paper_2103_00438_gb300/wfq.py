@@ -17,7 +17,7 @@ WFQ_OK = 0
 STATUS = {0: "WFQ_OK", -1: "WFQ_EINVAL", -2: "WFQ_ESINGULAR", -3: "WFQ_ENOMEM", -4: "WFQ_ENOCONV",
           -5: "WFQ_EBREAKDOWN", -6: "WFQ_ETIMEOUT", -7: "WFQ_ECUDA", -8: "WFQ_EUNSUPPORTED"}
 STORE_FP64, STORE_BF16X2, STORE_F32X2, STORE_F32X2_SYM = 1, 2, 4, 8
-PREC_FP64, PREC_MIXED, PREC_DF = 0, 1, 2
+PREC_FP64, PREC_MIXED, PREC_DF, PREC_FMM = 0, 1, 2, 3
 
 # every symbol include/wfq.h declares
 EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches", "wfq_build_geometry",
@@ -25,8 +25,8 @@ EXPORTS = ["wfq_create", "wfq_destroy", "wfq_last_error", "wfq_kernel_launches",
            "wfq_geometry_info", "wfq_apply", "wfq_rhs", "wfq_solve_gmres", "wfq_solve_gmres_shifted", "wfq_solve_qmr",
            "wfq_polarizability", "wfq_profile", "wfq_profile_read", "wfq_apply_mixed_noalloc",
            "wfq_server_create", "wfq_server_submit", "wfq_server_poll", "wfq_server_destroy",
-           "wfq_memory_stats", "wfq_cross_section"]
-KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE, KT_ORTHO, KT_RESIDUAL, KT_DGEMV_DF = 0, 1, 2, 3, 4, 5
+           "wfq_memory_stats", "wfq_cross_section", "wfq_fmm_build", "wfq_fmm_info"]
+KT_GEMM_MIXED, KT_DAPPLY_FP64, KT_SPARSE, KT_ORTHO, KT_RESIDUAL, KT_DGEMV_DF, KT_FMM = 0, 1, 2, 3, 4, 5, 6
 
 
 class WfqError(RuntimeError):
@@ -93,6 +93,8 @@ def load(path: str | None = None):
     L.wfq_server_destroy.argtypes = [_P]
     L.wfq_profile.argtypes = [_P, INT]
     L.wfq_memory_stats.argtypes = [_P, _P]
+    L.wfq_fmm_build.argtypes = [_P, INT]
+    L.wfq_fmm_info.argtypes = [_P, _P]
     L.wfq_cross_section.argtypes = [_P, I64, _P, INT, _P, D, _P, _P, _P, _P]
     L.wfq_profile_read.argtypes = [_P, INT, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
     for name in EXPORTS:
@@ -216,6 +218,15 @@ class Geometry:
                                        ctypes.byref(h)))
         self.h = h
 
+    def fmm_build(self, order: int = 6):
+        """Tree and operators of the fast-multipole D product (wfq_apply with PREC_FMM)."""
+        _check(_lib.wfq_fmm_build(self.h, int(order)))
+
+    def fmm_info(self):
+        out = np.zeros(7, dtype=np.int64)
+        _check(_lib.wfq_fmm_info(self.h, out.ctypes.data))
+        return dict(zip(("dim", "depth", "order", "leaves", "boxes", "interactions", "near"), (int(v) for v in out)))
+
     def info(self):
         n, nnz, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(_lib.wfq_geometry_info(self.h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(b)))
@@ -235,9 +246,9 @@ class Geometry:
     # ---------------------------------------------------------------- calls
 
     def apply(self, omega, x, y, prec: int = PREC_FP64, stream=None):
-        """y = (A - z(omega_c) I) x; x, y: (n, ncplx) complex128 (FP64) / complex64 (MIXED)."""
+        """y = (A - z(omega_c) I) x; x, y: (n, ncplx) complex128 (FP64, DF) / complex64 (MIXED, FMM)."""
         om = _host_f64(np.atleast_1d(omega))
-        dt = np.complex64 if prec == PREC_MIXED else np.complex128
+        dt = np.complex64 if prec in (PREC_MIXED, PREC_FMM) else np.complex128
         x, px = _buf(x, dt, self.n, self.n * len(om), False, "x")
         y, py = _buf(y, dt, self.n, self.n * len(om), True, "y")
         _check(_lib.wfq_apply(self.h, len(om), _ptr(om), px, py, int(prec), _stream_handle(stream)))

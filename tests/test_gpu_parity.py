@@ -451,6 +451,28 @@ def test_shifted_gmres_bitwise_repeatable_across_contexts(W, S):
     assert np.array_equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("store", ["bf16x2", "matrix_free"])
+def test_mixed_apply_bitwise_repeatable_across_contexts(W, S, store):
+    """The tensor-core GEMMs (stored planes and matrix-free) are autotuned per context: the
+    first product of a shape times several pipeline depths and keeps the fastest.  The depth
+    changes only how far loads run ahead, so two contexts agree bitwise whichever depth
+    each picked, product after product."""
+    xyz = S.random_cluster(2300, seed=12)
+    p = dict(S.carbon_params(1.2), r0=2.7)
+    om = S.ev(np.linspace(0.2, 1.6, 24))
+    x = S.random_complex((len(xyz), 24), seed=13).astype(np.complex64)
+    out = []
+    for _ in range(2):
+        c = W.Context(0)
+        g = W.Geometry(c, xyz, p, store=W.STORE_BF16X2 if store == "bf16x2" else 0)
+        ys = [g.apply(om, x, np.empty_like(x), prec=W.PREC_MIXED) for _ in range(2)]
+        assert np.array_equal(ys[0], ys[1])
+        out.append(ys[1])
+        g.close()
+        c.close()
+    assert np.array_equal(out[0], out[1])
+
+
 def test_shifted_gmres_symmetric_tiles_equal_full_planes(W, ctx, S):
     """The symmetric tiled D (each stored tile used for D_IJ x_J and D_IJ^T x_I) gives the
     same solves as the full FP32 pair planes up to double-float rounding: 3000 atoms, 47 tile

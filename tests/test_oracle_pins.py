@@ -419,6 +419,18 @@ def test_qmr_pin_catches_planted_mistakes(orc, S, tmp_path, plant):
     assert _qmr_pin_deviation(sysm.operator(), sysm, z, R, M, library=orc.load(str(so))) > 1e-6
 
 
+def test_rhs_rows_equal_the_assembled_rhs(orc, S):
+    # the brute-force row form of Eq. 13 used by residual audits of large structures
+    xyz = S.random_cluster(300, seed=8)
+    p = _params(S, r0=2.7)
+    K = orc.kbar_matrix(xyz, p)
+    rows = np.arange(0, 300, 7)
+    for k in (KX, np.array([0.6, 0.0, 0.8])):
+        R = orc.rhs_dense(xyz, K, k, E0=0.7)
+        np.testing.assert_allclose(orc.rhs_rows(xyz, p, k, rows, E0=0.7), R[rows], rtol=0,
+                                   atol=1e-13 * np.abs(R).max())
+
+
 def test_qmr_on_the_fly_equals_stored(orc, S):
     xyz = S.random_cluster(90, seed=17)
     p = _params(S, r0=2.7)
