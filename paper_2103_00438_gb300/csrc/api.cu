@@ -147,7 +147,7 @@ static int galloc(wfq_geom *g, T **p, size_t count) {
 }
 
 static void free_geom(wfq_geom *g) {
-    void *ptrs[] = {g->xyz, g->atom64, g->atom32, g->atomdf, g->eta, g->rowptr, g->col,
+    void *ptrs[] = {g->xyz, g->atom64, g->atom32, g->atom32p, g->atomdf, g->eta, g->rowptr, g->col,
                     g->val64, g->val32, g->D64, g->Dhi, g->Dlo, g->Dfh, g->Dfl,
                     g->Dsym, g->sym_items, g->sym_item_start, g->elem};
     for (void *p : ptrs)
@@ -381,6 +381,7 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     if ((rc = galloc(g, &g->xyz, 3 * n))) return bail(rc);
     if ((rc = galloc(g, &g->atom64, n))) return bail(rc);
     if ((rc = galloc(g, &g->atom32, g->npad))) return bail(rc);
+    if ((rc = galloc(g, &g->atom32p, g->npad))) return bail(rc);
     if ((rc = galloc(g, &g->atomdf, 2 * n))) return bail(rc);
     if ((rc = galloc(g, &g->eta, n))) return bail(rc);
     if ((rc = galloc(g, &g->rowptr, n + 1))) return bail(rc);
@@ -425,6 +426,15 @@ int wfq_build_geometry(wfq_ctx *ctx, int64_t n, const double *xyz, const double 
     if ((rc = up(g->xyz, xyz, sizeof(double) * 3 * n))) return bail(rc);
     if ((rc = up(g->atom64, a64.data(), sizeof(atom64_t) * n))) return bail(rc);
     if ((rc = up(g->atom32, a32.data(), sizeof(float4) * g->npad))) return bail(rc);
+    {
+        std::vector<float4> a32p(g->npad);   // npad is a multiple of 128: whole pairs
+        for (int64_t k = 0; k < g->npad; k += 2) {
+            const float4 a = a32[k], b = a32[k + 1];
+            a32p[k] = make_float4(a.x, b.x, a.y, b.y);
+            a32p[k + 1] = make_float4(a.z, b.z, a.w, b.w);
+        }
+        if ((rc = up(g->atom32p, a32p.data(), sizeof(float4) * g->npad))) return bail(rc);
+    }
     if ((rc = up(g->atomdf, adf.data(), sizeof(float4) * 2 * n))) return bail(rc);
     if ((rc = up(g->eta, eta_h.data(), sizeof(double) * n))) return bail(rc);
     if ((rc = up(g->rowptr, rowptr.data(), sizeof(int64_t) * (n + 1)))) return bail(rc);

@@ -158,6 +158,9 @@ struct wfq_geom {
     double *xyz = nullptr;      // n x 3
     wfq::atom64_t *atom64 = nullptr;  // (x, y, z, width), n
     float4 *atom32 = nullptr;   // (x, y, z, width), npad (padding: far away, width 1)
+    float4 *atom32p = nullptr;  // the same records by atom pairs (2k, 2k + 1): (x0, x1, y0, y1),
+                                // (z0, z1, w0, w1) -- one float4 per atom, npad; the matrix-free
+                                // generator reads them as packed FP32x2 operands
     float4 *atomdf = nullptr;   // 2 per atom: (xh, xl, yh, yl), (zh, zl, width, 0) float pairs
     double *eta = nullptr;      // n
     wfq::elem64_t *elem = nullptr;   // BEM geometries: n element records

@@ -28,7 +28,8 @@ constexpr int MF_THREADS = 64 + 32 * MF_GEN_WARPS;
 
 struct MfParams {
     Params p;
-    const float4 *atoms;   // npad records (x, y, z, width); rows/columns >= n are zero in D
+    const float4 *atoms;     // npad records (x, y, z, width); rows/columns >= n are zero in D
+    const float4 *atoms_p;   // the same by atom pairs: (x0, x1, y0, y1), (z0, z1, w0, w1)
 };
 
 // D_ik of Eq. 3 in FP32.  Beyond r = 4 sigma, erfc < 1.6e-8 and erf(r/sigma) rounds to 1
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
                 const uint32_t fb = smem_u32(full + s);
                 const uint32_t ab = smem_u32(atoms_full + s);
                 mbar_expect_tx(ab, MF_ATOM_BYTES);
-                bulk_load(base + atoms_off, mp.atoms + (int64_t)kb * BK, MF_ATOM_BYTES, ab);
+                bulk_load(base + atoms_off, mp.atoms_p + (int64_t)kb * BK, MF_ATOM_BYTES, ab);
                 mbar_expect_tx(fb, b_tx);
                 for (int j = 0; j < p.nsplit; ++j) {
                     tma_load_2d(base + 2 * A_BYTES + (uint32_t)(j * p.nchunk * ROWB), &tm_xhi, fb, kb * BK,
@@ -218,6 +219,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
             const bool row_ok = gi < p.n;
             const float wa2 = ai.w * ai.w;
             const float eta_i = eta_from_w / ai.w;
+            // the row atom as packed operands (the same value in both lanes)
+            const float2 aix2 = make_float2(ai.x, ai.x), aiy2 = make_float2(ai.y, ai.y);
+            const float2 aiz2 = make_float2(ai.z, ai.z), wa2_2 = make_float2(wa2, wa2);
             for (; u < seg_end; ++u, ++it) {
                 const int s = (int)(it % p.stages);
                 const uint32_t ph = (uint32_t)((it / p.stages) & 1);
@@ -233,19 +237,30 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
                 {
                     const int kb0 = k0 + kc * 8;
                     float dv[8], r2v[8], s2v[8];
-                    bool near = false;
+                    // the chunk's 8 atoms as 4 pairs, two k-atoms per packed FP32x2 operation
+                    // (per lane the same operations, in the same order, as for one atom)
+                    float nmin = 1.f;   // min of r^2 - 16 s^2 over the chunk: < 0 for a near pair
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 xy = atoms_s[kc * 8 + 2 * q], zw = atoms_s[kc * 8 + 2 * q + 1];
+                        const float2 dx = __fadd2_rn(aix2, make_float2(-xy.x, -xy.y));
+                        const float2 dy = __fadd2_rn(aiy2, make_float2(-xy.z, -xy.w));
+                        const float2 dz = __fadd2_rn(aiz2, make_float2(-zw.x, -zw.y));
+                        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                        const float2 bw = make_float2(zw.z, zw.w);
+                        const float2 s2 = __ffma2_rn(bw, bw, wa2_2);
+                        r2v[2 * q] = r2.x;
+                        r2v[2 * q + 1] = r2.y;
+                        s2v[2 * q] = s2.x;
+                        s2v[2 * q + 1] = s2.y;
                         // far pairs: 1/r from one rsqrt (erf(r/sigma) rounds to 1 in FP32)
-                        const float4 b = atoms_s[kc * 8 + e];
-                        const float dx = ai.x - b.x, dy = ai.y - b.y, dz = ai.z - b.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float s2 = fmaf(b.w, b.w, wa2);
-                        r2v[e] = r2;
-                        s2v[e] = s2;
-                        dv[e] = rsqrt_mufu(r2);
-                        near = near || (r2 < 16.0f * s2);
+                        dv[2 * q] = rsqrt_mufu(r2.x);
+                        dv[2 * q + 1] = rsqrt_mufu(r2.y);
+                        // r^2 - 16 s^2 in one rounding: its sign is that of r^2 - 16 s^2 itself
+                        const float2 t = __ffma2_rn(s2, make_float2(-16.f, -16.f), r2);
+                        nmin = fminf(nmin, fminf(t.x, t.y));
                     }
+                    const bool near = nmin < 0.f;
                     // near pairs (rare: only tiles close to the diagonal) take the erf branch,
                     // entered by a warp only when one of its lanes needs it
                     if (__any_sync(0xffffffffu, near)) {
@@ -268,9 +283,10 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
                         const uint32_t h = bf16x2_rn(dv[e], dv[e + 1]);
-                        const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
+                        const float2 h01 = make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xffff0000u));
+                        const float2 d = __fadd2_rn(make_float2(dv[e], dv[e + 1]), make_float2(-h01.x, -h01.y));
                         hw[e >> 1] = h;
-                        lw[e >> 1] = bf16x2_rn(dv[e] - h0, dv[e + 1] - h1);
+                        lw[e >> 1] = bf16x2_rn(d.x, d.y);
                     }
                     // 64-byte swizzle: 16-byte chunk index XOR (row / 2) mod 4
                     const uint32_t off = (uint32_t)row * 64u + (uint32_t)((kc ^ ((row >> 1) & 3)) * 16);
@@ -335,7 +351,8 @@ __global__ void __launch_bounds__(MF_THREADS, 1)
 }
 
 // One launch for a group of <= 512 accumulator columns.
-inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad, const __nv_bfloat16 *Xhi,
+inline cudaError_t launch_group_mf(const float4 *atoms, const float4 *atoms_p, int64_t n, int64_t npad,
+                                   const __nv_bfloat16 *Xhi,
                                    const __nv_bfloat16 *Xlo, int cpad, float *U, int64_t ldu, int64_t ncols,
                                    int num_sms, int *err, cudaStream_t s, std::string *msg,
                                    int stages_req = 0) {
@@ -362,6 +379,7 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
     p.err = err;
     p.timeout_ns = 4000000000ull;
     mp.atoms = atoms;
+    mp.atoms_p = atoms_p;
     if (p.stages < 2 || p.nchunk % 16 != 0 || p.nchunk > 256) {
         if (msg) *msg = "gemm_mf: unsupported column count";
         return cudaErrorInvalidValue;
@@ -379,7 +397,8 @@ inline cudaError_t launch_group_mf(const float4 *atoms, int64_t n, int64_t npad,
     return cudaGetLastError();
 }
 
-inline cudaError_t gemm3_mf(const float4 *atoms, int64_t n, int64_t npad, const __nv_bfloat16 *Xhi,
+inline cudaError_t gemm3_mf(const float4 *atoms, const float4 *atoms_p, int64_t n, int64_t npad,
+                            const __nv_bfloat16 *Xhi,
                             const __nv_bfloat16 *Xlo, int64_t cpad, float *U, int64_t ldu, int num_sms, int *err,
                             cudaStream_t s, int *launches, std::string *msg, int stages_req = 0) {
     if (npad % BM != 0 || cpad % 32 != 0 || cpad < ldu || ldu < 1) {
@@ -393,7 +412,7 @@ inline cudaError_t gemm3_mf(const float4 *atoms, int64_t n, int64_t npad, const 
     for (int64_t c0 = 0; c0 < ldu; c0 += 512) {
         const int group = (int)((cpad - c0) < 512 ? (cpad - c0) : 512);
         const int64_t valid = (ldu - c0) < group ? (ldu - c0) : group;
-        cudaError_t e = launch_group_mf(atoms, n, npad, Xhi + c0 * npad, Xlo + c0 * npad, group, U + c0, ldu, valid,
+        cudaError_t e = launch_group_mf(atoms, atoms_p, n, npad, Xhi + c0 * npad, Xlo + c0 * npad, group, U + c0, ldu, valid,
                                         num_sms, err, s, msg, stages_req);
         if (e != cudaSuccess) return e;
         if (launches) ++*launches;

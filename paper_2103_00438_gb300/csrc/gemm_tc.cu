@@ -71,13 +71,13 @@ int gemm_3xbf16_mf(const wfq_geom *g, int64_t cpad, const __nv_bfloat16 *Xhi, co
     // shapes take the deepest pipeline without a trial
     const int st = g->npad > 262144 ? 0 : tuned_stages(g, gemm_key(2, g->npad, cpad), s, [&](int stg) {
         int l = 0;
-        const cudaError_t e = tc::gemm3_mf(g->atom32, g->n, g->npad, Xhi, Xlo, cpad, U, ldu, g->ctx->num_sms,
+        const cudaError_t e = tc::gemm3_mf(g->atom32, g->atom32p, g->n, g->npad, Xhi, Xlo, cpad, U, ldu, g->ctx->num_sms,
                                            g->ctx->dev_err, s, &l, nullptr, stg);
         for (int i = 0; i < l; ++i) note_launch();
         return e;
     });
     KScope ks(g->ctx, WFQ_KT_GEMM_MIXED, s, 6.0 * (double)g->n * (double)g->n * (double)ldu);
-    cudaError_t e = tc::gemm3_mf(g->atom32, g->n, g->npad, Xhi, Xlo, cpad, U, ldu, g->ctx->num_sms, g->ctx->dev_err,
+    cudaError_t e = tc::gemm3_mf(g->atom32, g->atom32p, g->n, g->npad, Xhi, Xlo, cpad, U, ldu, g->ctx->num_sms, g->ctx->dev_err,
                                  s, &launches, &msg, st);
     for (int i = 0; i < launches; ++i) note_launch();
     if (e != cudaSuccess) {
