@@ -461,11 +461,14 @@ __global__ void __launch_bounds__(256) k_dotf_df(int64_t n, int64_t C, const flo
 }
 
 int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
+    if (!g->D64 && !g->Dfh && g->Dsym && cc <= 4) return d_apply_pairs_df(g, cc, X, U, s);
     if (!g->D64 && !g->Dfh) {
         // matrix-free double-float product
         WFQ_TRY(require_wfq(g));
         const int64_t n = g->n, C = 2 * cc;
-        if (C <= 2) return d_apply_fp64(g, cc, X, U, s);
+        // few columns: the double-float GEMV that regenerates D per product (the shifted
+        // solver's matrix-free product, up to 4 real vectors per launch)
+        if (C <= 8) return d_apply_mf_gemv_df(g, cc, X, U, s);
         KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);
         const double *x = reinterpret_cast<const double *>(X);
         double *u = reinterpret_cast<double *>(U);
@@ -499,6 +502,9 @@ int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cuda
 
 int d_apply_fp64(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
     const int64_t n = g->n, C = 2 * cc;
+    // no FP64 D but stored float pairs: their double-float product (2^-48 per product, on
+    // the FP32 pipes and at 8 or 4 bytes per entry) instead of regenerating D in FP64
+    if (!g->D64 && (g->Dfh || g->Dsym) && C <= 8) return d_apply_pairs_df(g, cc, X, U, s);
     const double *x = reinterpret_cast<const double *>(X);
     double *u = reinterpret_cast<double *>(U);
     KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);

@@ -263,6 +263,14 @@ int d_apply_fp64(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cu
 // the FP64 kernels.  Used for the refinement residual of mixed-precision solves.
 int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s);
 
+// U = D X for at most 4 complex columns with double-float products (~2^-48 per product)
+// from the stored float pairs (full planes or symmetric tiles) -- the FP64-grade product of
+// geometries that store no FP64 D (shifted.cu).
+int d_apply_pairs_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s);
+// The same for a geometry with no stored D: D regenerated per product in double-float
+// (the shifted solver's matrix-free GEMV), at most 4 complex columns.
+int d_apply_mf_gemv_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s);
+
 // U = D X with 3 bf16 products and FP32 accumulation: stored bf16 planes when present,
 // else tiles generated from the coordinates (matrix-free).
 // scratch: at least mixed_scratch_bytes(g, cc) bytes of device memory.

@@ -831,7 +831,91 @@ struct Arnoldi {
     }
 };
 
+// Real column r of an atom-major complex block X (n x cc; r = 2c + 0/1 for the real and
+// imaginary parts of column c) split into direction-major float pairs xh/xl [C][n].
+__global__ void k_cols_split(int64_t n, int C, const double *__restrict__ X, float *__restrict__ xh,
+                             float *__restrict__ xl) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * C) return;
+    const int64_t r = e / n, i = e - r * n;
+    df_split(X[i * C + r], xh[e], xl[e]);
+}
+
+// U (atom-major complex block, real column r at i * C + r) = Ud [C][n]
+__global__ void k_cols_gather(int64_t n, int C, const double *__restrict__ Ud, double *__restrict__ U) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * C) return;
+    const int64_t i = e / C, r = e - i * C;
+    U[e] = Ud[r * n + i];
+}
+
 }  // namespace
+
+int d_apply_pairs_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
+    const int64_t n = g->n;
+    const int C = (int)(2 * cc);
+    if (!(g->Dfh || g->Dsym) || C > 8) return fail(WFQ_EUNSUPPORTED, "float-pair product: needs stored pairs, <= 4 columns");
+    DevBuf<float> xh, xl;
+    DevBuf<double> ud, rowpart, colpart;
+    WFQ_TRY(xh.alloc(g->ctx, (size_t)n * C, s));
+    WFQ_TRY(xl.alloc(g->ctx, (size_t)n * C, s));
+    WFQ_TRY(ud.alloc(g->ctx, (size_t)n * C, s));
+    k_cols_split<<<nblk(n * C), 256, 0, s>>>(n, C, reinterpret_cast<const double *>(X), xh.ptr, xl.ptr);
+    note_launch();
+    KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);
+    if (g->Dfh) {
+        for (int d0 = 0; d0 < C; d0 += 4) {
+            const int cg = std::min(4, C - d0);
+            launch_dgemv_c<true>(cg, 0, n, g->ldf, g->Dfh, g->Dfl, nullptr, xh.ptr + (int64_t)d0 * n,
+                                 xl.ptr + (int64_t)d0 * n, ud.ptr + (int64_t)d0 * n, s);
+            note_launch();
+        }
+    } else {
+        const int64_t T = g->sym_nt;
+        WFQ_TRY(rowpart.alloc(g->ctx, (size_t)g->sym_nitems * kSymTile * 4 * 2, s));
+        WFQ_TRY(colpart.alloc(g->ctx, (size_t)(T * (T + 1) / 2) * kSymTile * 4 * 2, s));
+        float2 *rp = reinterpret_cast<float2 *>(rowpart.ptr), *cp = reinterpret_cast<float2 *>(colpart.ptr);
+        for (int d0 = 0; d0 < C; d0 += 4) {
+            const int cg = std::min(4, C - d0);
+            const float *ph = xh.ptr + (int64_t)d0 * n, *pxl = xl.ptr + (int64_t)d0 * n;
+            const unsigned items = (unsigned)g->sym_nitems;
+            switch (cg) {
+                case 1: k_dsymv_df<1><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rp, cp); break;
+                case 2: k_dsymv_df<2><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rp, cp); break;
+                case 3: k_dsymv_df<3><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rp, cp); break;
+                default: k_dsymv_df<4><<<items, 256, 0, s>>>(n, T, g->Dsym, g->sym_items, ph, pxl, rp, cp); break;
+            }
+            note_launch();
+            k_dsymv_finish<<<nblk(n * cg), 256, 0, s>>>(n, cg, T, g->sym_item_start, rp, cp, ud.ptr + (int64_t)d0 * n);
+            note_launch();
+        }
+    }
+    k_cols_gather<<<nblk(n * C), 256, 0, s>>>(n, C, ud.ptr, reinterpret_cast<double *>(U));
+    note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
+}
+
+int d_apply_mf_gemv_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
+    const int64_t n = g->n;
+    const int C = (int)(2 * cc);
+    if (C > 8) return fail(WFQ_EUNSUPPORTED, "matrix-free double-float GEMV: at most 4 complex columns");
+    DevBuf<float> xh, xl;
+    DevBuf<double> ud;
+    WFQ_TRY(xh.alloc(g->ctx, (size_t)n * C, s));
+    WFQ_TRY(xl.alloc(g->ctx, (size_t)n * C, s));
+    WFQ_TRY(ud.alloc(g->ctx, (size_t)n * C, s));
+    k_cols_split<<<nblk(n * C), 256, 0, s>>>(n, C, reinterpret_cast<const double *>(X), xh.ptr, xl.ptr);
+    note_launch();
+    KScope ks(g->ctx, WFQ_KT_DAPPLY_FP64, s, 2.0 * (double)n * (double)n * (double)C);
+    for (int d0 = 0; d0 < C; d0 += 4)
+        WFQ_TRY(d_gemv_df_mf(g, std::min(4, C - d0), xh.ptr + (int64_t)d0 * n, xl.ptr + (int64_t)d0 * n,
+                             ud.ptr + (int64_t)d0 * n, s));
+    k_cols_gather<<<nblk(n * C), 256, 0, s>>>(n, C, ud.ptr, reinterpret_cast<double *>(U));
+    note_launch();
+    WFQ_CUDA(cudaGetLastError());
+    return WFQ_OK;
+}
 
 size_t shifted_footprint(const wfq_geom *g, int64_t ncols, int ndir, int m) {
     if (m <= 0) m = 600;

@@ -142,6 +142,30 @@ def test_apply_double_float_within_derived_bound(W, ctx, orc, S, n, ncplx, store
     assert worst <= TAU_DF
 
 
+@pytest.mark.parametrize("n,ncplx,store", [(1000, 1, "f32x2"), (1333, 4, "f32x2"), (1100, 2, "f32x2sym"),
+                                           (1333, 3, "f32x2sym"), (200, 1, "f32x2sym")])
+def test_apply_fp64_from_float_pairs_within_double_float_bound(W, ctx, orc, S, n, ncplx, store):
+    """A geometry that stores only the float-pair D (full planes or symmetric tiles) applies
+    WFQ_PREC_FP64 with the double-float product of those pairs (up to four columns): the
+    double-float bound of the test above, TAU_DF = 8 * 2^-48 * sqrt(N)."""
+    TAU_DF = 8 * 2.0 ** -48 * np.sqrt(n)
+    xyz = S.random_cluster(n, seed=n + 9)
+    p = _carbon(S, r0=2.7)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2 if store == "f32x2" else W.STORE_F32X2_SYM)
+    sysm = orc.System(xyz, p)
+    om = S.ev(np.linspace(0.2, 1.9, ncplx))
+    x = S.random_complex((n, ncplx), seed=12)
+    y = np.empty_like(x)
+    g.apply(om, x, y, prec=W.PREC_FP64)
+    worst = 0.0
+    for c in range(ncplx):
+        z = sysm.z(om[c])
+        ref = _oracle_apply(orc, sysm, z, x[:, c])
+        worst = max(worst, float(np.max(np.abs(y[:, c] - ref) / _mixed_bound(sysm, z, x[:, c]))))
+    print("FP64 apply from float pairs: max |dy| / unit bound =", worst)
+    assert worst <= TAU_DF
+
+
 @pytest.mark.parametrize("n,ncplx", [(1000, 1), (1337, 3), (2049, 8), (129, 2), (3000, 40)])
 def test_apply_mixed_matrix_free_within_derived_bound(W, ctx, orc, S, n, ncplx):
     """Matrix-free tensor-core path: D tiles generated in FP32 from the coordinates and
