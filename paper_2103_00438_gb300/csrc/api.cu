@@ -1,7 +1,11 @@
 // C ABI of libwfq (include/wfq.h): argument checking, handle management, host/device
 // staging, dispatch to the kernels.
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -15,6 +19,27 @@ static std::atomic<int64_t> g_allocs{0};   // device allocations requested by th
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
+
+bool trace_on() {
+    static const bool on = [] {
+        const char *e = std::getenv("WFQ_TRACE");
+        return e != nullptr && *e != '\0' && std::strcmp(e, "0") != 0;
+    }();
+    return on;
+}
+
+void trace(const char *fmt, ...) {
+    if (!trace_on()) return;
+    static const auto t0 = std::chrono::steady_clock::now();
+    const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::fprintf(stderr, "[wfq %9.3f s] %s\n", t, buf);
+    std::fflush(stderr);
+}
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 const char *get_error() { return g_last_error.c_str(); }

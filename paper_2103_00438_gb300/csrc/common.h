@@ -18,6 +18,10 @@ namespace wfq {
 // ------------------------------------------------------------------ errors
 
 void set_error(const std::string &msg);
+// Solver progress on stderr (one line per restart cycle, escalation and continuation) when
+// the environment variable WFQ_TRACE is set and not "0"; off otherwise.
+bool trace_on();
+void trace(const char *fmt, ...) __attribute__((format(printf, 1, 2)));
 const char *get_error();
 
 struct Status {

@@ -23,6 +23,17 @@
 
 namespace wfq {
 
+// FP64-grade product inside the solvers' FP64 iterations and residuals. With no FP64 D
+// stored, the double-float product (~2^-48 per product, on the FP32 pipes: float pairs
+// read from the stored planes or tiles for few columns, D regenerated per product
+// otherwise) instead of D regenerated in FP64: on GB300's FP64 rate the latter is ~8 s per
+// 192-column product at 1.5e5 atoms and ~100 s per 32-column product at 10^6 atoms, the
+// double-float forms 4 to 6 times less.
+static int solver_fp64_product(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
+    if (!g->D64 && g->op == OP_WFQ) return d_apply_df(g, cc, X, U, s);
+    return d_apply_fp64(g, cc, X, U, s);
+}
+
 // ------------------------------------------------------------------ complex helpers
 
 __device__ __forceinline__ double2 ld2(const double2 *p) { return *p; }
@@ -595,7 +606,7 @@ struct Common {
         if (residual_df)
             WFQ_TRY(d_apply_df(g, na, xa.ptr, Ua.ptr, s));
         else
-            WFQ_TRY(d_apply_fp64(g, na, xa.ptr, Ua.ptr, s));
+            WFQ_TRY(solver_fp64_product(g, na, xa.ptr, Ua.ptr, s));
         WFQ_TRY(sparse_shift_fp64(g, na, Ua.ptr, xa.ptr, za.ptr, Ya.ptr, s));
         k_residual<<<nblocks(tot), 256, 0, s>>>(tot, Ba.ptr, Ya.ptr, ra.ptr); note_launch();
         WFQ_CUDA(cudaGetLastError());
@@ -717,12 +728,19 @@ struct GmresOut {
     int cycles = 0;
 };
 
-// A column of the mixed solve whose FP64 true residual shrank by less than this factor in
-// each of STAGNATION_CYCLES consecutive refinement cycles (its operator error times the
-// conditioning of A - zI is not small, or its residual sits at the rounding floor of the
-// double-float residual) leaves the mixed solve and is finished in plain FP64.
+// A column of the mixed solve leaves it, to be finished in plain FP64, when its FP64 true
+// residual shrank by less than STAGNATION_RATIO in each of STAGNATION_CYCLES consecutive
+// refinement cycles while the inner solve had reached its own target (GMRES: the mixed
+// operator's residual estimate below FLOOR_GAP times the true residual; QMR: the column
+// converged in the inner run): the operator error times the conditioning of A - zI is not
+// small, or the residual sits at the rounding floor of the double-float residual.  A cycle
+// that ended with the inner solve short of its target shows slow Krylov convergence, which
+// FP64 iterations would repeat at many times the cost: such a column escalates only after
+// SLOW_CYCLES consecutive slow cycles.
 constexpr double STAGNATION_RATIO = 0.5;
 constexpr int STAGNATION_CYCLES = 2;
+constexpr double FLOOR_GAP = 0.25;
+constexpr int SLOW_CYCLES = 20;
 constexpr int FLOOR_CYCLES = 5;
 
 template <class VT>
@@ -779,7 +797,8 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
     std::vector<double2> g_h;
     std::vector<int> jd_h;
     std::vector<double> prev_exact(cc, -1.0);   // last FP64 relative residual per column
-    std::vector<int> esc, flat_cycles(cc, 0);
+    std::vector<int> esc, flat_cycles(cc, 0), slow_cycles(cc, 0);
+    std::vector<double> inner_est(cc, -1.0);   // mixed: last cycle's inner residual estimate (absolute)
 
     for (;;) {
         if (exact) {
@@ -789,9 +808,11 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
                 keep.reserve(still.size());
                 for (int c : still) {
                     const bool slow = prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c];
-                    flat_cycles[c] = slow ? flat_cycles[c] + 1 : 0;
+                    const bool floor = inner_est[c] >= 0.0 && inner_est[c] < FLOOR_GAP * cm.res_h[c] * cm.bn_h[c];
+                    flat_cycles[c] = slow && floor ? flat_cycles[c] + 1 : 0;
+                    slow_cycles[c] = slow ? slow_cycles[c] + 1 : 0;
                     prev_exact[c] = cm.res_h[c];
-                    if (flat_cycles[c] >= STAGNATION_CYCLES)
+                    if (flat_cycles[c] >= STAGNATION_CYCLES || slow_cycles[c] >= SLOW_CYCLES)
                         esc.push_back(c);
                     else
                         keep.push_back(c);
@@ -811,6 +832,13 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
                     if (flat_cycles[c] < FLOOR_CYCLES) keep.push_back(c);
                 }
                 still.swap(keep);
+            }
+            if (trace_on()) {
+                double worst = 0.0;
+                for (int c : act) worst = std::max(worst, cm.res_h[c]);
+                trace("gmres(%d) %s cycle %d: %zu of %zu columns active, %zu escalated, %d steps, max true "
+                      "rel. residual %.3e", m, mixed ? "mixed" : "fp64", cycles, still.size(), act.size(), esc.size(),
+                      total, worst);
             }
             if (still.empty() || total >= a.max_iter) break;
             if (still.size() != act.size()) WFQ_TRY(cm.narrow(act, still));
@@ -839,7 +867,7 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
                 WFQ_TRY(sparse_shift_fp32(g, na, U32.ptr, reinterpret_cast<const float2 *>(vj), cm.za.ptr,
                                           reinterpret_cast<float2 *>(w), s));
             } else {
-                WFQ_TRY(d_apply_fp64(g, na, reinterpret_cast<const double2 *>(vj), cm.Ua.ptr, s));
+                WFQ_TRY(solver_fp64_product(g, na, reinterpret_cast<const double2 *>(vj), cm.Ua.ptr, s));
                 WFQ_TRY(sparse_shift_fp64(g, na, cm.Ua.ptr, reinterpret_cast<const double2 *>(vj), cm.za.ptr,
                                           reinterpret_cast<double2 *>(w), s));
             }
@@ -899,15 +927,18 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
             WFQ_CUDA(cudaMemcpyAsync(jd_h.data(), jdone.ptr, sizeof(int) * na, cudaMemcpyDeviceToHost, s));
             WFQ_CUDA(cudaStreamSynchronize(s));
             far = true;
-            for (int64_t k = 0; k < na && far; ++k) {
+            for (int64_t k = 0; k < na; ++k) {
                 const double2 gk = g_h[(size_t)jd_h[k] * na + k];
                 const double est = std::sqrt(gk.x * gk.x + gk.y * gk.y);
+                inner_est[act[k]] = est;
                 if (!(est > 1e-3 * cm.bn_h[act[k]])) far = false;
             }
         }
         if (far) {
             WFQ_TRY(cm.mixed_residual(a.q, na, xs32.ptr, U32.ptr, y32.ptr, scratch.ptr));
             exact = false;
+            trace("gmres(%d) mixed cycle %d: all %lld columns above 1e-3 |R|, mixed-operator residual", m, cycles,
+                  (long long)na);
         } else {
             WFQ_TRY(cm.true_residual(a.q, na));
             exact = true;
@@ -943,6 +974,8 @@ static int continue_columns(wfq_geom *g, const SolveArgs &a, const std::vector<i
                             const std::vector<double> &res, const std::vector<int> &iters, int prec, int m,
                             cudaStream_t s) {
     const int64_t ne = (int64_t)cols.size(), n = g->n, cc = (int64_t)res.size();
+    trace("continuing %lld of %lld columns by GMRES(%d) at %s", (long long)ne, (long long)cc, m,
+          prec == WFQ_PREC_MIXED ? "mixed precision" : "FP64");
     int used = 0;
     for (int c : cols) used = std::max(used, iters[c]);
     if (a.max_iter - used < 1) return fail(WFQ_ENOCONV, "iteration limit reached before rel_tol in some column");
@@ -1211,7 +1244,8 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *o
     // below sees every column regularly
     const int cycle_cap = mixed ? (a.refine_every > 0 ? a.refine_every : 300) : INT32_MAX;
     std::vector<double> prev_exact(cc, -1.0);
-    std::vector<int> flat(cc, 0), esc;
+    std::vector<int> flat(cc, 0), slow_runs(cc, 0), esc;
+    std::vector<char> inner_done(cc, 0);   // mixed: the column converged in the last inner run
     for (;;) {
         WFQ_TRY(cm.classify(act, a.rel_tol, still));
         // columns whose QMR broke down leave the active set; a mixed solve hands them, and
@@ -1220,14 +1254,21 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *o
         for (int c : still) {
             if (mixed && out) {
                 const bool slow = prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c];
-                flat[c] = slow ? flat[c] + 1 : 0;
+                flat[c] = slow && inner_done[c] ? flat[c] + 1 : 0;
+                slow_runs[c] = slow ? slow_runs[c] + 1 : 0;
                 prev_exact[c] = cm.res_h[c];
-                if (brk_h[c] || flat[c] >= STAGNATION_CYCLES) {
+                if (brk_h[c] || flat[c] >= STAGNATION_CYCLES || slow_runs[c] >= SLOW_CYCLES) {
                     esc.push_back(c);
                     continue;
                 }
             }
             if (!brk_h[c]) keep.push_back(c);
+        }
+        if (trace_on()) {
+            double worst = 0.0;
+            for (int c : act) worst = std::max(worst, cm.res_h[c]);
+            trace("qmr %s restart %d: %zu of %zu columns active, %zu escalated, %d steps, max true rel. residual "
+                  "%.3e", mixed ? "mixed" : "fp64", cycles, keep.size(), act.size(), esc.size(), total, worst);
         }
         if (keep.empty() || total >= a.max_iter) break;
         if (keep.size() != act.size()) WFQ_TRY(cm.narrow(act, keep));
@@ -1243,7 +1284,7 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *o
             if (mixed)
                 return d_apply_mixed(g, na, reinterpret_cast<const float2 *>(v), reinterpret_cast<float2 *>(u),
                                      scratch.ptr, s);
-            return d_apply_fp64(g, na, reinterpret_cast<const double2 *>(v), reinterpret_cast<double2 *>(u), s);
+            return solver_fp64_product(g, na, reinterpret_cast<const double2 *>(v), reinterpret_cast<double2 *>(u), s);
         };
         auto sparse = [&](const VT *u, const VT *x, VT *yv) -> int {
             if (mixed)
@@ -1296,6 +1337,7 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *o
         for (int64_t k = 0; k < na; ++k) {
             iters_h[act[k]] += tmp_i[k];
             if (b_a[k]) brk_h[act[k]] = 1;
+            inner_done[act[k]] = done_h[k] != 0;
         }
         ++cycles;
         WFQ_TRY(cm.true_residual(a.q, na));

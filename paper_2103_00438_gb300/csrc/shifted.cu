@@ -344,15 +344,27 @@ void launch_dgemv_c(int cg, int tiling, int64_t n, int64_t ld, const float *Fh, 
 }
 
 // W[d][i] = sum_p Kbar_ip (U[d][j_p] - U[d][i]) = ((Kbar - P) U)_i  (Eq. 16-17), FP64, for
-// directions d0 .. d0 + CG - 1.  One warp per row: the lanes stride over the row's
-// neighbours (coalesced CSR reads, each entry read once for all CG directions), then sum
-// in a fixed butterfly order.
-// LPR lanes per row (32 for long sodium rows, 8 for the ~50-entry carbon rows).
+// directions d0 .. d0 + CG - 1.  LPR lanes per row (32 for long sodium rows, 8 for the
+// ~50-entry carbon rows): the lanes stride over the row's neighbours (coalesced CSR reads,
+// each entry read once for all CG directions), then sum in a fixed butterfly order.
+// With `partial` set, the block then also forms the first Gram-Schmidt pass's partial dots
+// of its SP_THREADS / LPR rows of W with the basis vectors V_0 .. V_{nv-1}:
+// partial[(block * nv + k) * C + d], one warp per (k, d) with the rows on the lanes, SP_QB
+// (k, d) pairs in flight per warp, each summed by a fixed butterfly.
+constexpr int SP_THREADS = 256;
+constexpr int SP_QB = 8;
 template <int CG, int LPR>
-__global__ void __launch_bounds__(256) k_sparse_real(int64_t n, int d0, const int64_t *__restrict__ rowptr,
-                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                     const double *__restrict__ U, double *__restrict__ W) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
+__global__ void __launch_bounds__(SP_THREADS) k_sparse_real(int64_t n, int d0, const int64_t *__restrict__ rowptr,
+                                                            const int32_t *__restrict__ col,
+                                                            const double *__restrict__ val,
+                                                            const double *__restrict__ U, double *__restrict__ W,
+                                                            const double *__restrict__ V, int64_t vstride, int nv,
+                                                            int C, double *__restrict__ partial) {
+    constexpr int RPB = SP_THREADS / LPR;   // rows per block
+    constexpr int RPL = (RPB + 31) / 32;    // rows per lane in the dot phase
+    constexpr int NW = SP_THREADS / 32;
+    __shared__ double ws[CG][RPB];
+    const int64_t i = ((int64_t)blockIdx.x * SP_THREADS + threadIdx.x) / LPR;
     const int lane = threadIdx.x & (LPR - 1);
     const bool row_ok = i < n;   // rows past n still join the shuffles below
     double ui[CG], acc[CG];
@@ -378,6 +390,44 @@ __global__ void __launch_bounds__(256) k_sparse_real(int64_t n, int d0, const in
     if (row_ok && lane == 0)
 #pragma unroll
         for (int d = 0; d < CG; ++d) W[(int64_t)(d0 + d) * n + i] = acc[d];
+    if (partial == nullptr) return;   // uniform over the block
+    if (lane == 0)
+#pragma unroll
+        for (int d = 0; d < CG; ++d) ws[d][threadIdx.x / LPR] = row_ok ? acc[d] : 0.0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
+    const int64_t rbase = (int64_t)blockIdx.x * RPB;
+    const int nq = nv * CG;
+    for (int q0 = warp * SP_QB; q0 < nq; q0 += NW * SP_QB) {
+        double v[SP_QB];
+#pragma unroll
+        for (int h = 0; h < SP_QB; ++h) {
+            v[h] = 0.0;
+            const int q = q0 + h;
+            if (q >= nq) continue;
+            const int k = q / CG, dd = q - k * CG;
+            const double *vk = V + (int64_t)k * vstride + (int64_t)(d0 + dd) * n + rbase;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int rr = wl + 32 * r;
+                if (rr < RPB && rbase + rr < n) v[h] += vk[rr] * ws[dd][rr];
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < SP_QB; ++h) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[h] += __shfl_xor_sync(0xffffffffu, v[h], off);
+        }
+        if (wl == 0) {
+#pragma unroll
+            for (int h = 0; h < SP_QB; ++h) {
+                const int q = q0 + h;
+                if (q >= nq) continue;
+                const int k = q / CG, dd = q - k * CG;
+                partial[((int64_t)blockIdx.x * nv + k) * C + d0 + dd] = v[h];
+            }
+        }
+    }
 }
 
 // W[d][i] = R[i * C + d]   (atom-major right-hand sides -> direction-major vectors)
@@ -455,33 +505,139 @@ __global__ void k_rdot_fin(int nrb, int nv, int C, int mode, const double *__res
     coef[o] = s;
 }
 
-// w[d][i] -= sum_{k < nv} coef[k * C + d] V_k[d][i].  A block takes 32 consecutive
-// elements; its 8 warps take the vectors k = warp, warp + 8, ... (coalesced 256-byte rows of
-// each V_k), and the 8 partial sums are added in a fixed order.
-constexpr int RU_SLICES = 8;
-__global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate(int64_t n, int C, int nv, const double *__restrict__ V,
-                                                            int64_t vstride, const double *__restrict__ coef,
-                                                            double *__restrict__ w) {
-    __shared__ double part[RU_SLICES][32];
+constexpr int RU_SLICES = 8;   // warps per block of the Gram-Schmidt updates
+constexpr int RU_EPL = 4;      // elements per lane: a block covers RU_ELEMS consecutive rows
+constexpr int RU_ELEMS = 32 * RU_EPL;
+
+// w[d][i] -= sum_{k < nv} coef[k * C + d] V_k[d][i] on a grid of (RU_ELEMS-row blocks,
+// directions): the block's 8 warps take the vectors k = warp, warp + 8, ... (each lane 4
+// rows 32 apart: coalesced 256-byte rows of V_k, two vectors in flight) and their 8 partial
+// sums are added in a fixed order.  Fused with the next step's reductions of the updated w:
+// NEXT_DOTS -- the partial dots of w with V_0 .. V_{nv-1} for the second Gram-Schmidt pass,
+// partial[(block * nv + k) * C + d]; NEXT_NORM -- the partial squared norm,
+// partial[block * C + d].  Fixed orders throughout.
+enum { NEXT_DOTS = 1, NEXT_NORM = 2 };
+template <int NEXT>
+__global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate_next(int64_t n, int C, int nv, const double *__restrict__ V,
+                                                                 int64_t vstride, const double *__restrict__ coef,
+                                                                 double *__restrict__ w, double *__restrict__ partial) {
+    __shared__ double part[RU_SLICES][RU_ELEMS];
+    __shared__ double wv[RU_ELEMS];
+    __shared__ double sqw[RU_ELEMS / 32];
     const int el = threadIdx.x & 31, sl = threadIdx.x >> 5;
-    const int64_t e = (int64_t)blockIdx.x * 32 + el;
-    double a0 = 0.0, a1 = 0.0;
-    if (e < n * C) {
-        const int d = (int)(e / n);
-        int k = sl;
-        for (; k + RU_SLICES < nv; k += 2 * RU_SLICES) {
-            a0 += coef[k * C + d] * V[(int64_t)k * vstride + e];
-            a1 += coef[(k + RU_SLICES) * C + d] * V[(int64_t)(k + RU_SLICES) * vstride + e];
-        }
-        if (k < nv) a0 += coef[k * C + d] * V[(int64_t)k * vstride + e];
-    }
-    part[sl][el] = a0 + a1;
-    __syncthreads();
-    if (sl == 0 && e < n * C) {
-        double t = 0.0;
+    const int d = blockIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * RU_ELEMS;
+    const double *Vd = V + (int64_t)d * n + i0;
+    double a[RU_EPL];
 #pragma unroll
-        for (int q = 0; q < RU_SLICES; ++q) t += part[q][el];
-        w[e] -= t;
+    for (int r = 0; r < RU_EPL; ++r) a[r] = 0.0;
+    int k = sl;
+    for (; k + RU_SLICES < nv; k += 2 * RU_SLICES) {
+        const double c0 = coef[k * C + d], c1 = coef[(k + RU_SLICES) * C + d];
+        const double *v0 = Vd + (int64_t)k * vstride, *v1 = v0 + (int64_t)RU_SLICES * vstride;
+#pragma unroll
+        for (int r = 0; r < RU_EPL; ++r) {
+            const int e = el + 32 * r;
+            if (i0 + e < n) a[r] += c0 * v0[e] + c1 * v1[e];
+        }
+    }
+    if (k < nv) {
+        const double c0 = coef[k * C + d];
+        const double *v0 = Vd + (int64_t)k * vstride;
+#pragma unroll
+        for (int r = 0; r < RU_EPL; ++r) {
+            const int e = el + 32 * r;
+            if (i0 + e < n) a[r] += c0 * v0[e];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RU_EPL; ++r) part[sl][el + 32 * r] = a[r];
+    __syncthreads();
+    if (threadIdx.x < RU_ELEMS) {   // warps 0 .. RU_EPL - 1: one row each
+        const int e = threadIdx.x;
+        double wn = 0.0;
+        if (i0 + e < n) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < RU_SLICES; ++q) t += part[q][e];
+            double *we = w + (int64_t)d * n + i0 + e;
+            wn = *we - t;
+            *we = wn;
+        }
+        wv[e] = wn;
+        if (NEXT == NEXT_NORM) {
+            double sq = wn * wn;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+            if (el == 0) sqw[sl] = sq;
+        }
+    }
+    __syncthreads();
+    if (NEXT == NEXT_NORM) {
+        if (threadIdx.x == 0) {
+            double sq = 0.0;
+#pragma unroll
+            for (int q = 0; q < RU_ELEMS / 32; ++q) sq += sqw[q];
+            partial[(int64_t)blockIdx.x * C + d] = sq;
+        }
+        return;
+    }
+    for (int k0 = sl; k0 < nv; k0 += 2 * RU_SLICES) {
+        double v[2] = {0.0, 0.0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kk = k0 + h * RU_SLICES;
+            if (kk >= nv) continue;
+            const double *vk = Vd + (int64_t)kk * vstride;
+#pragma unroll
+            for (int r = 0; r < RU_EPL; ++r) {
+                const int e = el + 32 * r;
+                if (i0 + e < n) v[h] += vk[e] * wv[e];
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+            v[1] += __shfl_xor_sync(0xffffffffu, v[1], off);
+        }
+        if (el == 0) {
+            partial[((int64_t)blockIdx.x * nv + k0) * C + d] = v[0];
+            if (k0 + RU_SLICES < nv) partial[((int64_t)blockIdx.x * nv + k0 + RU_SLICES) * C + d] = v[1];
+        }
+    }
+}
+
+// The norms of the C directions from their nrb partial squares (every block reduces them
+// in the same fixed order: lane-strided sums, a butterfly), H(j + 1, j) = hn[d] = norm
+// (block 0), then v = w / norm with v's float-pair split, as k_rscale.  Four elements
+// per thread.
+__global__ void k_rscale_norm(int64_t n, int C, int nrb, const double *__restrict__ partial, int m, int j,
+                              double *__restrict__ H, double *__restrict__ hn, const double *__restrict__ w,
+                              double *__restrict__ v, float *__restrict__ xh, float *__restrict__ xl) {
+    extern __shared__ double nrm[];   // [C]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = warp; d < C; d += blockDim.x / 32) {
+        double sv = 0.0;
+        for (int rb = lane; rb < nrb; rb += 32) sv += partial[(int64_t)rb * C + d];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+        if (lane == 0) {
+            const double nr = sqrt(sv);
+            nrm[d] = nr;
+            if (blockIdx.x == 0) {
+                H[((int64_t)d * m + j) * (m + 1) + j + 1] = nr;
+                hn[d] = nr;
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const int64_t e = ((int64_t)blockIdx.x * 4 + q) * blockDim.x + threadIdx.x;
+        if (e >= n * C) break;
+        const double h = nrm[e / n];
+        const double t = h > 0.0 ? w[e] / h : 0.0;
+        v[e] = t;
+        df_split(t, xh[e], xl[e]);
     }
 }
 
@@ -679,6 +835,8 @@ struct Arnoldi {
     int nrb;
     DevBuf<float> xh, xl;
     DevBuf<double> U, partial, coef;
+    DevBuf<double> partial_f;   // partial reductions of the fused kernels (sparse + dots, update + dots / norm)
+    int nrb_s = 0, nbru = 0;
     DevBuf<float2> rowpart, colpart;   // symmetric product partial sums
 
     int init(wfq_geom *geom, int ndir, int m, cudaStream_t stream) {
@@ -692,6 +850,10 @@ struct Arnoldi {
         WFQ_TRY(xl.alloc(g->ctx, (size_t)n * C, s));
         WFQ_TRY(U.alloc(g->ctx, (size_t)n * C, s));
         WFQ_TRY(partial.alloc(g->ctx, (size_t)nrb * (m + 1) * C, s));
+        const int rpb_s = SP_THREADS / sparse_lpr();
+        nrb_s = (int)((n + rpb_s - 1) / rpb_s);
+        nbru = (int)((n + RU_ELEMS - 1) / RU_ELEMS);
+        WFQ_TRY(partial_f.alloc(g->ctx, (size_t)std::max(nrb_s, nbru) * (m + 1) * C, s));
         WFQ_TRY(coef.alloc(g->ctx, (size_t)(m + 1) * C, s));
         if (g->Dsym && !g->Dfh) {
             const int64_t T = g->sym_nt, cg = std::min<int64_t>(C, 4);
@@ -792,22 +954,36 @@ struct Arnoldi {
         return WFQ_OK;
     }
 
-    // w = (Kbar - P) u; BEM geometries (A = the stored operator itself): w = u
-    int sparse(const double *u, double *w) {
+    // lanes per row of the sparse term: a full warp for long (sodium) rows, 8 for carbon rows
+    int sparse_lpr() const { return g->nnz > 128 * n ? 32 : 8; }
+
+    // w = (Kbar - P) u; BEM geometries (A = the stored operator itself): w = u.  With V set,
+    // also the first Gram-Schmidt pass's partial dots of w with V_0 .. V_{nv-1} (partial_f,
+    // nrb_s row blocks); returns in *fused whether they were formed (not for BEM or long
+    // rows).
+    int sparse(const double *u, double *w, const double *V = nullptr, int64_t vstride = 0, int nv = 0,
+               bool *fused = nullptr) {
         KScope ks(g->ctx, WFQ_KT_SPARSE, s);
+        if (fused) *fused = false;
         if (g->op == OP_BEM) {
             WFQ_CUDA(cudaMemcpyAsync(w, u, sizeof(double) * n * C, cudaMemcpyDeviceToDevice, s));
             return WFQ_OK;
         }
-        const bool wide = g->nnz > 128 * n;   // long rows: a full warp per row
-        const unsigned blocks = nblk(n * (wide ? 32 : 8));
+        const bool wide = sparse_lpr() == 32;
+        const unsigned blocks = nblk(n * (wide ? 32 : 8), SP_THREADS);
+        // long (sodium) rows leave 8 rows per block, too few for the dots: those take
+        // the separate dot kernel
+        double *pf = V && !wide ? partial_f.ptr : nullptr;
+        if (fused) *fused = pf != nullptr;
         for (int d0 = 0; d0 < C; d0 += 4) {
             const int cg = std::min(4, C - d0);
-#define WFQ_SP(CC)                                                                                   \
-    if (wide)                                                                                        \
-        k_sparse_real<CC, 32><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w);     \
-    else                                                                                             \
-        k_sparse_real<CC, 8><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w);
+#define WFQ_SP(CC)                                                                                            \
+    if (wide)                                                                                                 \
+        k_sparse_real<CC, 32><<<blocks, SP_THREADS, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w, V, vstride, nv, \
+                                                     C, pf);                                                  \
+    else                                                                                                      \
+        k_sparse_real<CC, 8><<<blocks, SP_THREADS, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w, V, vstride, nv,  \
+                                                    C, pf);
             switch (cg) {
                 case 1: WFQ_SP(1) break;
                 case 2: WFQ_SP(2) break;
@@ -1013,16 +1189,35 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         double *dvj = DV.ptr + (int64_t)j * vstride;
         double *w = V.ptr + (int64_t)(j + 1) * vstride;
         WFQ_TRY(ar.dmul(dvj));
-        WFQ_TRY(ar.sparse(dvj, w));
+        // w = (Kbar - P) D v_j with the first pass's partial dots formed on the way; each
+        // update of the two classical Gram-Schmidt passes forms the partial reductions of the
+        // next step (the second pass's dots, then the norm); 8 launches per step with the
+        // D product and the Givens step (12 with a launch per reduction)
+        bool fused = false;
+        WFQ_TRY(ar.sparse(dvj, w, V.ptr, vstride, j + 1, &fused));
         {
             KScope ko(ctx, WFQ_KT_ORTHO, s);
-            for (int pass = 0; pass < 2; ++pass) {
-                WFQ_TRY(ar.dots(V.ptr, vstride, j + 1, w, pass == 0 ? RF_SET : RF_ADD, m, j, H.ptr, hn.ptr));
-                k_rupdate<<<nblk(n * C, 32), 32 * RU_SLICES, 0, s>>>(n, (int)C, j + 1, V.ptr, vstride, ar.coef.ptr, w);
+            const int nv = j + 1;
+            if (fused) {
+                k_rdot_fin<<<nblk((int64_t)nv * C * 32), 256, 0, s>>>(ar.nrb_s, nv, (int)C, RF_SET, ar.partial_f.ptr, m,
+                                                                      j, H.ptr, ar.coef.ptr, hn.ptr);
                 note_launch();
+            } else {
+                WFQ_TRY(ar.dots(V.ptr, vstride, nv, w, RF_SET, m, j, H.ptr, hn.ptr));
             }
-            WFQ_TRY(ar.dots(w, 0, 1, w, RF_NORM, m, j, H.ptr, hn.ptr));
-            k_rscale<<<nblk(n * C), 256, 0, s>>>(n, (int)C, hn.ptr, w, w, ar.xh.ptr, ar.xl.ptr); note_launch();
+            k_rupdate_next<NEXT_DOTS><<<dim3((unsigned)ar.nbru, (unsigned)C), 32 * RU_SLICES, 0, s>>>(
+                n, (int)C, nv, V.ptr, vstride, ar.coef.ptr, w, ar.partial_f.ptr);
+            note_launch();
+            k_rdot_fin<<<nblk((int64_t)nv * C * 32), 256, 0, s>>>(ar.nbru, nv, (int)C, RF_ADD, ar.partial_f.ptr, m, j,
+                                                                  H.ptr, ar.coef.ptr, hn.ptr);
+            note_launch();
+            k_rupdate_next<NEXT_NORM><<<dim3((unsigned)ar.nbru, (unsigned)C), 32 * RU_SLICES, 0, s>>>(
+                n, (int)C, nv, V.ptr, vstride, ar.coef.ptr, w, ar.partial_f.ptr);
+            note_launch();
+            k_rscale_norm<<<nblk(n * C, 1024), 256, sizeof(double) * C, s>>>(n, (int)C, ar.nbru, ar.partial_f.ptr, m,
+                                                                             j, H.ptr, hn.ptr, w, w, ar.xh.ptr,
+                                                                             ar.xl.ptr);
+            note_launch();
             WFQ_CUDA(cudaEventRecord(side.fork, s));
             WFQ_CUDA(cudaStreamWaitEvent(side.st, side.fork, 0));
             k_shift_givens<<<nblk(nc, PER_COLUMN_BLOCK), PER_COLUMN_BLOCK, 0, side.st>>>(st, j); note_launch();
@@ -1046,6 +1241,8 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
     WFQ_CUDA(cudaMemcpyAsync(jd_h.data(), jdone.ptr, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
     WFQ_CUDA(cudaStreamSynchronize(s));
 
+    trace("shifted gmres: %d Arnoldi steps for %lld columns (%lld directions)", jlast + 1, (long long)nc,
+          (long long)C);
     // FP64 true residual of every column; the ones above tol continue in block GMRES(50)
     return finish_columns(g, a, jd_h, 50, dq.ptr, s);
 }

@@ -11,6 +11,7 @@ Tolerances:
   * mixed solves (FP64 refinement): the acceptance bar -- alpha relative error <= 1e-6 and
     FP64 true residual <= 1e-8 relative, the residual re-measured by the oracle.
 """
+import os
 import numpy as np
 import pytest
 
@@ -535,6 +536,32 @@ def test_shifted_gmres_matrix_free_matches_lu(W, ctx, orc, S):
             assert st[c]["rel_residual"] <= 1e-10 and st[c]["restarts"] == 0
 
 
+@pytest.mark.parametrize("solver", ["gmres", "qmr"])
+def test_fp64_solvers_matrix_free_match_lu(W, ctx, orc, S, solver):
+    """No D stored: the FP64 block GMRES and QMR iterations and their true residuals take
+    the double-float products that regenerate D per product (~2^-48 each, far below the
+    requested residual); every column still equals its LU solve."""
+    xyz = S.nanotube(5, 5, 30)          # 600 atoms
+    p = S.carbon_params(1.04)
+    g = W.Geometry(ctx, xyz, p, store=0)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.2, 1.3])
+    dirs = np.eye(3)[:2]
+    if solver == "gmres":
+        q, st, status = g.solve_gmres(om, dirs, m=60, rel_tol=1e-10, max_iter=3000, prec=W.PREC_FP64)
+    else:
+        q, st, status = g.solve_qmr(om, dirs, rel_tol=1e-10, max_iter=3000, prec=W.PREC_FP64)
+    assert status == "WFQ_OK", st
+    al = g.polarizability(q)
+    for f in range(2):
+        for d in range(2):
+            c = f * 2 + d
+            q_lu, _ = sysm.solve(om[f], dirs[d], method="lu")
+            a_ref = orc.alpha(xyz, q_lu)
+            assert np.abs(al[c] - a_ref).max() <= 1e-8 * np.abs(a_ref).max(), (solver, f, d)
+            assert st[c]["rel_residual"] <= 1e-10
+
+
 # ----------------------------------------------------------------------------- edge cases
 
 def test_edge_single_atom_and_dimer(W, ctx, orc, S):
@@ -680,3 +707,25 @@ def test_full_size_mixed_apply_sampled_rows(W, ctx, orc, S, name):
         print(name, "column", c, "max |dy| / unit bound =", ratio)
         assert ratio <= TAU_MIXED
     g.close()
+
+
+def test_solver_trace_on_stderr(S):
+    """WFQ_TRACE=1: the solvers report each restart cycle on stderr; unset, nothing."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_2103_00438_gb300 import wfq, structures as S\n"
+            "ctx = wfq.Context(0)\n"
+            "g = wfq.Geometry(ctx, S.honeycomb_flake(6), S.carbon_params(1.51), store=wfq.STORE_BF16X2)\n"
+            "q, st, status = g.solve_gmres(S.ev([0.6]), [[1.0, 0, 0]], m=20, rel_tol=1e-8, prec=wfq.PREC_MIXED)\n"
+            "assert status == 'WFQ_OK', st\n")
+    for flag, expect in (("1", True), ("0", False)):
+        env = dict(os.environ, WFQ_TRACE=flag)
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                           timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        lines = [ln for ln in r.stderr.splitlines() if ln.startswith("[wfq")]
+        if expect:
+            assert any("gmres(20) mixed cycle" in ln for ln in lines), r.stderr[-2000:]
+        else:
+            assert not lines
