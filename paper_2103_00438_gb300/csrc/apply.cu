@@ -461,7 +461,10 @@ __global__ void __launch_bounds__(256) k_dotf_df(int64_t n, int64_t C, const flo
 }
 
 int d_apply_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
-    if (!g->D64 && !g->Dfh && g->Dsym && cc <= 4) return d_apply_pairs_df(g, cc, X, U, s);
+    // symmetric float-pair tiles: read them, 4 real vectors per pass (the product that
+    // regenerates D from the coordinates' float pairs held the true residual of a 1.5e5-atom
+    // sodium sphere near 5e-7, where the stored pairs reach 5e-9)
+    if (!g->D64 && !g->Dfh && g->Dsym) return d_apply_pairs_df(g, cc, X, U, s);
     if (!g->D64 && !g->Dfh) {
         // matrix-free double-float product
         WFQ_TRY(require_wfq(g));

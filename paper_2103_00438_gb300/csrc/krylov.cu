@@ -517,6 +517,14 @@ struct Common {
     DevBuf<double> bnorm_a;
     std::vector<double> bn_h, res_h;   // ||B_c||, final relative residual per column
     bool residual_df = false;          // double-float D products in the true residual
+    bool residual_exact = false;       // FP64 D products in the true residual (overrides residual_df)
+
+    // A mixed solve on a geometry with no stored D takes its residuals from the double-float
+    // product that regenerates D; where those hold a column's residual at a floor, the
+    // residual can switch to D regenerated in FP64.
+    bool can_tighten_residual() const {
+        return residual_df && !residual_exact && !g->D64 && !g->Dfh && !g->Dsym && g->op == OP_WFQ;
+    }
 
     int init(wfq_geom *geom, const SolveArgs &a, cudaStream_t stream) {
         g = geom;
@@ -603,10 +611,10 @@ struct Common {
         KScope ks(g->ctx, WFQ_KT_RESIDUAL, s);
         const uint32_t tot = (uint32_t)(n * na);
         k_gather<double2, double2><<<nblocks(tot), 256, 0, s>>>(tot, (uint32_t)na, cc, idx.ptr, x, xa.ptr); note_launch();
-        if (residual_df)
+        if (residual_df && !residual_exact)
             WFQ_TRY(d_apply_df(g, na, xa.ptr, Ua.ptr, s));
         else
-            WFQ_TRY(solver_fp64_product(g, na, xa.ptr, Ua.ptr, s));
+            WFQ_TRY(d_apply_fp64(g, na, xa.ptr, Ua.ptr, s));
         WFQ_TRY(sparse_shift_fp64(g, na, Ua.ptr, xa.ptr, za.ptr, Ya.ptr, s));
         k_residual<<<nblocks(tot), 256, 0, s>>>(tot, Ba.ptr, Ya.ptr, ra.ptr); note_launch();
         WFQ_CUDA(cudaGetLastError());
@@ -806,16 +814,31 @@ static int gmres_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut 
             if (mixed && out) {
                 std::vector<int> keep;
                 keep.reserve(still.size());
+                bool tighten = false;
                 for (int c : still) {
                     const bool slow = prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c];
                     const bool floor = inner_est[c] >= 0.0 && inner_est[c] < FLOOR_GAP * cm.res_h[c] * cm.bn_h[c];
                     flat_cycles[c] = slow && floor ? flat_cycles[c] + 1 : 0;
                     slow_cycles[c] = slow ? slow_cycles[c] + 1 : 0;
                     prev_exact[c] = cm.res_h[c];
+                    if (flat_cycles[c] >= STAGNATION_CYCLES && cm.can_tighten_residual()) tighten = true;
                     if (flat_cycles[c] >= STAGNATION_CYCLES || slow_cycles[c] >= SLOW_CYCLES)
                         esc.push_back(c);
                     else
                         keep.push_back(c);
+                }
+                if (tighten) {
+                    // the floor is the residual's: recompute it with D in FP64 and carry on
+                    // in mixed precision with every column of this cycle
+                    esc.resize(esc.size() - (still.size() - keep.size()));
+                    cm.residual_exact = true;
+                    std::fill(flat_cycles.begin(), flat_cycles.end(), 0);
+                    std::fill(slow_cycles.begin(), slow_cycles.end(), 0);
+                    std::fill(prev_exact.begin(), prev_exact.end(), -1.0);
+                    trace("gmres(%d) mixed cycle %d: residual floor of the regenerated double-float D; residuals "
+                          "from D in FP64 from here", m, cycles);
+                    WFQ_TRY(cm.true_residual(a.q, (int64_t)act.size()));
+                    continue;
                 }
                 still.swap(keep);
             } else if (!mixed) {
@@ -1251,18 +1274,35 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *o
         // columns whose QMR broke down leave the active set; a mixed solve hands them, and
         // the columns that stalled over two restarts, to FP64 GMRES afterwards
         std::vector<int> keep;
+        const size_t esc0 = esc.size();
+        bool tighten = false;
         for (int c : still) {
             if (mixed && out) {
                 const bool slow = prev_exact[c] >= 0.0 && cm.res_h[c] > STAGNATION_RATIO * prev_exact[c];
                 flat[c] = slow && inner_done[c] ? flat[c] + 1 : 0;
                 slow_runs[c] = slow ? slow_runs[c] + 1 : 0;
                 prev_exact[c] = cm.res_h[c];
+                if (flat[c] >= STAGNATION_CYCLES && !brk_h[c] && cm.can_tighten_residual()) tighten = true;
                 if (brk_h[c] || flat[c] >= STAGNATION_CYCLES || slow_runs[c] >= SLOW_CYCLES) {
                     esc.push_back(c);
                     continue;
                 }
             }
             if (!brk_h[c]) keep.push_back(c);
+        }
+        if (tighten) {
+            // the floor is the residual's: recompute it with D in FP64 and carry on in mixed
+            // precision (columns whose QMR broke down still leave)
+            esc.erase(std::remove_if(esc.begin() + (std::ptrdiff_t)esc0, esc.end(), [&](int c) { return !brk_h[c]; }),
+                      esc.end());
+            cm.residual_exact = true;
+            std::fill(flat.begin(), flat.end(), 0);
+            std::fill(slow_runs.begin(), slow_runs.end(), 0);
+            std::fill(prev_exact.begin(), prev_exact.end(), -1.0);
+            trace("qmr mixed restart %d: residual floor of the regenerated double-float D; residuals from D in "
+                  "FP64 from here", cycles);
+            WFQ_TRY(cm.true_residual(a.q, (int64_t)act.size()));
+            continue;
         }
         if (trace_on()) {
             double worst = 0.0;

@@ -347,24 +347,13 @@ void launch_dgemv_c(int cg, int tiling, int64_t n, int64_t ld, const float *Fh, 
 // directions d0 .. d0 + CG - 1.  LPR lanes per row (32 for long sodium rows, 8 for the
 // ~50-entry carbon rows): the lanes stride over the row's neighbours (coalesced CSR reads,
 // each entry read once for all CG directions), then sum in a fixed butterfly order.
-// With `partial` set, the block then also forms the first Gram-Schmidt pass's partial dots
-// of its SP_THREADS / LPR rows of W with the basis vectors V_0 .. V_{nv-1}:
-// partial[(block * nv + k) * C + d], one warp per (k, d) with the rows on the lanes, SP_QB
-// (k, d) pairs in flight per warp, each summed by a fixed butterfly.
-constexpr int SP_THREADS = 256;
-constexpr int SP_QB = 8;
+// (Forming the first Gram-Schmidt pass's dots here as well, from the block's rows, measured
+// 2x slower than this kernel and k_rdot_part apart: a block holds too few rows for them.)
 template <int CG, int LPR>
-__global__ void __launch_bounds__(SP_THREADS) k_sparse_real(int64_t n, int d0, const int64_t *__restrict__ rowptr,
-                                                            const int32_t *__restrict__ col,
-                                                            const double *__restrict__ val,
-                                                            const double *__restrict__ U, double *__restrict__ W,
-                                                            const double *__restrict__ V, int64_t vstride, int nv,
-                                                            int C, double *__restrict__ partial) {
-    constexpr int RPB = SP_THREADS / LPR;   // rows per block
-    constexpr int RPL = (RPB + 31) / 32;    // rows per lane in the dot phase
-    constexpr int NW = SP_THREADS / 32;
-    __shared__ double ws[CG][RPB];
-    const int64_t i = ((int64_t)blockIdx.x * SP_THREADS + threadIdx.x) / LPR;
+__global__ void __launch_bounds__(256) k_sparse_real(int64_t n, int d0, const int64_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                     const double *__restrict__ U, double *__restrict__ W) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
     const int lane = threadIdx.x & (LPR - 1);
     const bool row_ok = i < n;   // rows past n still join the shuffles below
     double ui[CG], acc[CG];
@@ -390,44 +379,6 @@ __global__ void __launch_bounds__(SP_THREADS) k_sparse_real(int64_t n, int d0, c
     if (row_ok && lane == 0)
 #pragma unroll
         for (int d = 0; d < CG; ++d) W[(int64_t)(d0 + d) * n + i] = acc[d];
-    if (partial == nullptr) return;   // uniform over the block
-    if (lane == 0)
-#pragma unroll
-        for (int d = 0; d < CG; ++d) ws[d][threadIdx.x / LPR] = row_ok ? acc[d] : 0.0;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
-    const int64_t rbase = (int64_t)blockIdx.x * RPB;
-    const int nq = nv * CG;
-    for (int q0 = warp * SP_QB; q0 < nq; q0 += NW * SP_QB) {
-        double v[SP_QB];
-#pragma unroll
-        for (int h = 0; h < SP_QB; ++h) {
-            v[h] = 0.0;
-            const int q = q0 + h;
-            if (q >= nq) continue;
-            const int k = q / CG, dd = q - k * CG;
-            const double *vk = V + (int64_t)k * vstride + (int64_t)(d0 + dd) * n + rbase;
-#pragma unroll
-            for (int r = 0; r < RPL; ++r) {
-                const int rr = wl + 32 * r;
-                if (rr < RPB && rbase + rr < n) v[h] += vk[rr] * ws[dd][rr];
-            }
-        }
-#pragma unroll
-        for (int h = 0; h < SP_QB; ++h) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v[h] += __shfl_xor_sync(0xffffffffu, v[h], off);
-        }
-        if (wl == 0) {
-#pragma unroll
-            for (int h = 0; h < SP_QB; ++h) {
-                const int q = q0 + h;
-                if (q >= nq) continue;
-                const int k = q / CG, dd = q - k * CG;
-                partial[((int64_t)blockIdx.x * nv + k) * C + d0 + dd] = v[h];
-            }
-        }
-    }
 }
 
 // W[d][i] = R[i * C + d]   (atom-major right-hand sides -> direction-major vectors)
@@ -835,8 +786,8 @@ struct Arnoldi {
     int nrb;
     DevBuf<float> xh, xl;
     DevBuf<double> U, partial, coef;
-    DevBuf<double> partial_f;   // partial reductions of the fused kernels (sparse + dots, update + dots / norm)
-    int nrb_s = 0, nbru = 0;
+    DevBuf<double> partial_f;   // partial reductions of the fused kernels (update + dots / norm)
+    int nbru = 0;
     DevBuf<float2> rowpart, colpart;   // symmetric product partial sums
 
     int init(wfq_geom *geom, int ndir, int m, cudaStream_t stream) {
@@ -850,10 +801,8 @@ struct Arnoldi {
         WFQ_TRY(xl.alloc(g->ctx, (size_t)n * C, s));
         WFQ_TRY(U.alloc(g->ctx, (size_t)n * C, s));
         WFQ_TRY(partial.alloc(g->ctx, (size_t)nrb * (m + 1) * C, s));
-        const int rpb_s = SP_THREADS / sparse_lpr();
-        nrb_s = (int)((n + rpb_s - 1) / rpb_s);
         nbru = (int)((n + RU_ELEMS - 1) / RU_ELEMS);
-        WFQ_TRY(partial_f.alloc(g->ctx, (size_t)std::max(nrb_s, nbru) * (m + 1) * C, s));
+        WFQ_TRY(partial_f.alloc(g->ctx, (size_t)nbru * (m + 1) * C, s));
         WFQ_TRY(coef.alloc(g->ctx, (size_t)(m + 1) * C, s));
         if (g->Dsym && !g->Dfh) {
             const int64_t T = g->sym_nt, cg = std::min<int64_t>(C, 4);
@@ -957,33 +906,22 @@ struct Arnoldi {
     // lanes per row of the sparse term: a full warp for long (sodium) rows, 8 for carbon rows
     int sparse_lpr() const { return g->nnz > 128 * n ? 32 : 8; }
 
-    // w = (Kbar - P) u; BEM geometries (A = the stored operator itself): w = u.  With V set,
-    // also the first Gram-Schmidt pass's partial dots of w with V_0 .. V_{nv-1} (partial_f,
-    // nrb_s row blocks); returns in *fused whether they were formed (not for BEM or long
-    // rows).
-    int sparse(const double *u, double *w, const double *V = nullptr, int64_t vstride = 0, int nv = 0,
-               bool *fused = nullptr) {
+    // w = (Kbar - P) u; BEM geometries (A = the stored operator itself): w = u
+    int sparse(const double *u, double *w) {
         KScope ks(g->ctx, WFQ_KT_SPARSE, s);
-        if (fused) *fused = false;
         if (g->op == OP_BEM) {
             WFQ_CUDA(cudaMemcpyAsync(w, u, sizeof(double) * n * C, cudaMemcpyDeviceToDevice, s));
             return WFQ_OK;
         }
         const bool wide = sparse_lpr() == 32;
-        const unsigned blocks = nblk(n * (wide ? 32 : 8), SP_THREADS);
-        // long (sodium) rows leave 8 rows per block, too few for the dots: those take
-        // the separate dot kernel
-        double *pf = V && !wide ? partial_f.ptr : nullptr;
-        if (fused) *fused = pf != nullptr;
+        const unsigned blocks = nblk(n * (wide ? 32 : 8));
         for (int d0 = 0; d0 < C; d0 += 4) {
             const int cg = std::min(4, C - d0);
-#define WFQ_SP(CC)                                                                                            \
-    if (wide)                                                                                                 \
-        k_sparse_real<CC, 32><<<blocks, SP_THREADS, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w, V, vstride, nv, \
-                                                     C, pf);                                                  \
-    else                                                                                                      \
-        k_sparse_real<CC, 8><<<blocks, SP_THREADS, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w, V, vstride, nv,  \
-                                                    C, pf);
+#define WFQ_SP(CC)                                                                                    \
+    if (wide)                                                                                         \
+        k_sparse_real<CC, 32><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w);      \
+    else                                                                                              \
+        k_sparse_real<CC, 8><<<blocks, 256, 0, s>>>(n, d0, g->rowptr, g->col, g->val64, u, w);
             switch (cg) {
                 case 1: WFQ_SP(1) break;
                 case 2: WFQ_SP(2) break;
@@ -1030,7 +968,7 @@ __global__ void k_cols_gather(int64_t n, int C, const double *__restrict__ Ud, d
 int d_apply_pairs_df(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
     const int64_t n = g->n;
     const int C = (int)(2 * cc);
-    if (!(g->Dfh || g->Dsym) || C > 8) return fail(WFQ_EUNSUPPORTED, "float-pair product: needs stored pairs, <= 4 columns");
+    if (!(g->Dfh || g->Dsym)) return fail(WFQ_EUNSUPPORTED, "float-pair product: needs stored pairs");
     DevBuf<float> xh, xl;
     DevBuf<double> ud, rowpart, colpart;
     WFQ_TRY(xh.alloc(g->ctx, (size_t)n * C, s));
@@ -1189,22 +1127,15 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         double *dvj = DV.ptr + (int64_t)j * vstride;
         double *w = V.ptr + (int64_t)(j + 1) * vstride;
         WFQ_TRY(ar.dmul(dvj));
-        // w = (Kbar - P) D v_j with the first pass's partial dots formed on the way; each
-        // update of the two classical Gram-Schmidt passes forms the partial reductions of the
-        // next step (the second pass's dots, then the norm); 8 launches per step with the
-        // D product and the Givens step (12 with a launch per reduction)
-        bool fused = false;
-        WFQ_TRY(ar.sparse(dvj, w, V.ptr, vstride, j + 1, &fused));
+        // w = (Kbar - P) D v_j, the first classical Gram-Schmidt pass's dots; each update of
+        // the two passes forms the partial reductions of the next step (the second pass's
+        // dots, then the norm): 9 launches per step with the D product and the Givens step
+        // (12 with a launch per reduction)
+        WFQ_TRY(ar.sparse(dvj, w));
         {
             KScope ko(ctx, WFQ_KT_ORTHO, s);
             const int nv = j + 1;
-            if (fused) {
-                k_rdot_fin<<<nblk((int64_t)nv * C * 32), 256, 0, s>>>(ar.nrb_s, nv, (int)C, RF_SET, ar.partial_f.ptr, m,
-                                                                      j, H.ptr, ar.coef.ptr, hn.ptr);
-                note_launch();
-            } else {
-                WFQ_TRY(ar.dots(V.ptr, vstride, nv, w, RF_SET, m, j, H.ptr, hn.ptr));
-            }
+            WFQ_TRY(ar.dots(V.ptr, vstride, nv, w, RF_SET, m, j, H.ptr, hn.ptr));
             k_rupdate_next<NEXT_DOTS><<<dim3((unsigned)ar.nbru, (unsigned)C), 32 * RU_SLICES, 0, s>>>(
                 n, (int)C, nv, V.ptr, vstride, ar.coef.ptr, w, ar.partial_f.ptr);
             note_launch();
