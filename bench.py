@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--store", default=None,
                     help="comma list of D storages overriding the workload's (fp64, bf16, f32x2, sym)")
     ap.add_argument("--m", type=int, default=50)
+    ap.add_argument("--other-warmup", type=int, default=None,
+                    help="untimed solves of each other solver form before its timed one (default: min(2, warmup))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true",
@@ -500,7 +502,8 @@ def run_ours(args, rank, world, dist):
                 continue
             saved = args.solver
             args.solver = name
-            for _ in range(max(1, min(2, args.warmup))):
+            ow = min(2, args.warmup) if args.other_warmup is None else args.other_warmup
+            for _ in range(max(0, ow)):
                 solve(q_other)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -611,7 +614,7 @@ def run_ours(args, rank, world, dist):
 def _summary(o):
     """The figures of a sub-run's JSON line that the default line carries."""
     keep = {"metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "accuracy", "latency",
-            "cpu_baseline", "gpu_launches"}
+            "cpu_baseline", "gpu_launches", "other_solvers"}
     out = {k: v for k, v in o.items() if k in keep}
     cfg = o.get("config", {})
     out["config"] = {k: cfg[k] for k in ("workload", "n_atoms", "columns", "requests", "solver", "path",
@@ -632,16 +635,20 @@ def _summary(o):
 def run_other_configs(args):
     """The other configurations' figures, carried by the default cnt20k line: the 1M-atom
     disk's matrix-free mixed apply (Gint/s against the derived ALU roof, sampled oracle
-    rows) and its fast-multipole apply (order 6), a shortened serving stream (p50/p99 latency; served over plain per-column FP64
-    GMRES on the same GPU) and one shifted-GMRES step of the 150k-atom sphere (FP32 pair
-    planes).  Each runs in its own context after the cnt20k geometry is freed."""
+    rows) and its fast-multipole apply (order 6), a shortened serving stream (p50/p99 latency;
+    served over plain per-column FP64 GMRES on the same GPU) and the 150k-atom sphere's
+    solver comparison at equal accuracy (96 columns to 1e-8: one shifted-GMRES step from the
+    symmetric FP32 pair tiles, then mixed QMR and mixed GMRES(30) on the bf16 planes beside
+    them, each timed once).  Each runs in its own context after the cnt20k geometry is
+    freed."""
     import torch
     plans = [
         ("disk1m_apply", dict(workload="disk1m", mode="apply", steps=2, warmup=1, no_e2e=True)),
         ("disk1m_fmm_apply", dict(workload="disk1m", mode="apply", fmm_order=6, steps=3, warmup=1, no_e2e=True)),
         ("serve_240_requests", dict(workload="serve", mode="serve", requests=240, warmup=1)),
-        ("sphere150k_shifted", dict(workload="sphere150k", mode="solve", solver="shifted", steps=1, warmup=1,
-                                    no_e2e=True, no_other_solvers=True, no_other_configs=True)),
+        ("sphere150k_solvers", dict(workload="sphere150k", mode="solve", solver="shifted", steps=1, warmup=1,
+                                    store="sym,bf16", other_solvers="qmr,gmres", m=30, other_warmup=0,
+                                    no_e2e=True, no_other_configs=True)),
     ]
     res = {}
     for key, kw in plans:
