@@ -60,7 +60,9 @@ __device__ __forceinline__ double2 c_div(double2 a, double2 b) {
 // vector) as much as by memory; which tiling overlaps the two best depends on N and on the
 // number of vectors, so the first product of each shape times all of them on the real
 // operands and keeps the fastest (autotune below).  A sweep at N = 20000 found 0.75-0.85 ms
-// per launch for these four and 0.9-1.4 ms for wider or 16-warp tilings.
+// per launch for these four and 0.9-1.4 ms for wider or 16-warp tilings.  Staging x by
+// asynchronous copies into two 512-column buffers, with each chunk's first D loads issued
+// ahead of the barrier, measured slower (0.728 vs 0.679 ms per cnt20k product).
 constexpr int GV_WARPS = 8;      // warps per block
 constexpr int GV_CHUNK = 1024;   // x entries staged in shared memory per step
 constexpr int GV_NTILINGS = 4;
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate_next(int64_t n, int 
         }
     }
     __syncthreads();
-    if (NEXT == NEXT_NORM) {
+    if constexpr (NEXT == NEXT_NORM) {
         if (threadIdx.x == 0) {
             double sq = 0.0;
 #pragma unroll
@@ -533,6 +535,7 @@ __global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate_next(int64_t n, int 
         }
         return;
     }
+    if constexpr (NEXT == NEXT_DOTS)
     for (int k0 = sl; k0 < nv; k0 += 2 * RU_SLICES) {
         double v[2] = {0.0, 0.0};
 #pragma unroll
