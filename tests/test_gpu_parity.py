@@ -117,18 +117,21 @@ def test_apply_mixed_within_derived_bound(W, ctx, orc, S, n, ncplx):
 
 
 @pytest.mark.parametrize("n,ncplx,store", [(1000, 3, "fp64"), (1333, 7, "fp64"), (2049, 40, "fp64"),
-                                           (1333, 7, "f32x2"), (2049, 40, "f32x2")])
+                                           (1333, 7, "f32x2"), (2049, 40, "f32x2"), (1333, 7, "sym"),
+                                           (2049, 40, "sym")])
 def test_apply_double_float_within_derived_bound(W, ctx, orc, S, n, ncplx, store):
     """Double-float D products: operands split into float pairs (48 significant bits),
     products and sums error-free up to ~2^-48 each, so per element
         |dy_i| <= TAU_DF * (sum_p Kbar_ip (s_i + s_j) + |z| |x_i|),  s = |D| |x|,
     with TAU_DF = 8 * 2^-48 * sqrt(N): rounding errors of 2^-48 per step that add up
     like a random walk over the N-term sum, with a factor 8 of margin.  D split from the
-    stored FP64 D, or read from the stored FP32 pair planes (the same 48-bit pair)."""
+    stored FP64 D, or read from the stored FP32 pair planes or symmetric pair tiles (the same
+    48-bit pair; the tiles four real columns per pass, for any number of columns)."""
     TAU_DF = 8 * 2.0 ** -48 * np.sqrt(n)
     xyz = S.random_cluster(n, seed=n + 5)
     p = _carbon(S, r0=2.7)
-    g = W.Geometry(ctx, xyz, p, store=W.STORE_FP64 if store == "fp64" else W.STORE_F32X2)
+    g = W.Geometry(ctx, xyz, p, store={"fp64": W.STORE_FP64, "f32x2": W.STORE_F32X2,
+                                       "sym": W.STORE_F32X2_SYM}[store])
     sysm = orc.System(xyz, p)
     om = S.ev(np.linspace(0.2, 1.9, ncplx))
     x = S.random_complex((n, ncplx), seed=11)
@@ -560,6 +563,33 @@ def test_fp64_solvers_matrix_free_match_lu(W, ctx, orc, S, solver):
             a_ref = orc.alpha(xyz, q_lu)
             assert np.abs(al[c] - a_ref).max() <= 1e-8 * np.abs(a_ref).max(), (solver, f, d)
             assert st[c]["rel_residual"] <= 1e-10
+
+
+@pytest.mark.parametrize("solver", ["gmres", "qmr"])
+def test_mixed_solvers_on_symmetric_pair_tiles_match_lu(W, ctx, orc, S, solver):
+    """The storage of the 150k-atom sphere's solver comparison: bf16 planes for the mixed
+    iterations, symmetric FP32 pair tiles for the refinement residuals (their double-float
+    product, four real columns per pass, 12 columns here); every column meets the acceptance
+    bar against its LU solve."""
+    xyz = S.nanotube(5, 5, 30)          # 600 atoms
+    p = S.carbon_params(1.04)
+    g = W.Geometry(ctx, xyz, p, store=W.STORE_F32X2_SYM | W.STORE_BF16X2)
+    sysm = orc.System(xyz, p)
+    om = S.ev([0.3, 0.9, 1.3, 1.8])
+    dirs = np.eye(3)
+    if solver == "gmres":
+        q, st, status = g.solve_gmres(om, dirs, m=30, rel_tol=1e-8, max_iter=4000, prec=W.PREC_MIXED)
+    else:
+        q, st, status = g.solve_qmr(om, dirs, rel_tol=1e-8, max_iter=4000, prec=W.PREC_MIXED)
+    assert status == "WFQ_OK", st
+    al = g.polarizability(q)
+    for f in range(len(om)):
+        for d in range(3):
+            c = f * 3 + d
+            q_lu, _ = sysm.solve(om[f], dirs[d], method="lu")
+            a_ref = orc.alpha(xyz, q_lu)
+            assert np.abs(al[c] - a_ref).max() <= 1e-6 * np.abs(a_ref).max(), (solver, f, d)
+            assert st[c]["rel_residual"] <= 1e-8
 
 
 # ----------------------------------------------------------------------------- edge cases
