@@ -62,7 +62,10 @@ __device__ __forceinline__ double2 c_div(double2 a, double2 b) {
 // operands and keeps the fastest (autotune below).  A sweep at N = 20000 found 0.75-0.85 ms
 // per launch for these four and 0.9-1.4 ms for wider or 16-warp tilings.  Staging x by
 // asynchronous copies into two 512-column buffers, with each chunk's first D loads issued
-// ahead of the barrier, measured slower (0.728 vs 0.679 ms per cnt20k product).
+// ahead of the barrier, measured slower (0.728 vs 0.679 ms per cnt20k product); so did
+// streaming D through shared memory by 2-D bulk tensor copies (a producer lane, a 4-stage
+// mbarrier ring of 8 or 16 rows x 256 columns, 8 consumer warps, 2 CTAs per SM): 2.24 and
+// 1.43 ms per cnt20k product.
 constexpr int GV_WARPS = 8;      // warps per block
 constexpr int GV_CHUNK = 1024;   // x entries staged in shared memory per step
 constexpr int GV_NTILINGS = 4;
