@@ -468,41 +468,20 @@ constexpr int RU_ELEMS = 32 * RU_EPL;
 // w[d][i] -= sum_{k < nv} coef[k * C + d] V_k[d][i] on a grid of (RU_ELEMS-row blocks,
 // directions): the block's 8 warps take the vectors k = warp, warp + 8, ... (each lane 4
 // rows 32 apart: coalesced 256-byte rows of V_k, two vectors in flight) and their 8 partial
-// sums are added in a fixed order.  With `pin` set, the coefficients are first finished
-// here from the nrb_in partial dots pin[(rb * nv + k) * C + d] of the pass before (every
-// block sums them in k_rdot_fin's order: lane-strided, then a butterfly; block 0 stores
-// them in column j of H), instead of read from coef.  Fused with the next step's
-// reductions of the updated w: NEXT_DOTS -- the partial dots of w with V_0 .. V_{nv-1} for
-// the second Gram-Schmidt pass, partial[(block * nv + k) * C + d]; NEXT_NORM -- the partial
-// squared norm, partial[block * C + d].  Fixed orders throughout.
+// sums are added in a fixed order.  Fused with the next step's reductions of the updated w:
+// NEXT_DOTS -- the partial dots of w with V_0 .. V_{nv-1} for the second Gram-Schmidt pass,
+// partial[(block * nv + k) * C + d]; NEXT_NORM -- the partial squared norm,
+// partial[block * C + d].  Fixed orders throughout.
 enum { NEXT_DOTS = 1, NEXT_NORM = 2 };
-constexpr int RU_FIN_MAX = 4096;   // most coefficients finished in shared memory (32 KiB)
 template <int NEXT>
 __global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate_next(int64_t n, int C, int nv, const double *__restrict__ V,
                                                                  int64_t vstride, const double *__restrict__ coef,
-                                                                 double *__restrict__ w, double *__restrict__ partial,
-                                                                 const double *__restrict__ pin, int nrb_in, int m,
-                                                                 int j, double *__restrict__ H) {
+                                                                 double *__restrict__ w, double *__restrict__ partial) {
     __shared__ double part[RU_SLICES][RU_ELEMS];
     __shared__ double wv[RU_ELEMS];
     __shared__ double sqw[RU_ELEMS / 32];
-    extern __shared__ double cs[];   // [nv] when pin is set
     const int el = threadIdx.x & 31, sl = threadIdx.x >> 5;
     const int d = blockIdx.y;
-    if (pin != nullptr) {   // uniform over the grid
-        for (int kk = sl; kk < nv; kk += RU_SLICES) {
-            double sv = 0.0;
-            for (int rb = el; rb < nrb_in; rb += 32) sv += pin[((int64_t)rb * nv + kk) * C + d];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
-            if (el == 0) {
-                cs[kk] = sv;
-                if (blockIdx.x == 0) H[((int64_t)d * m + j) * (m + 1) + kk] = sv;
-            }
-        }
-        __syncthreads();
-    }
-    auto cf = [&](int kk) -> double { return pin != nullptr ? cs[kk] : coef[kk * C + d]; };
     const int64_t i0 = (int64_t)blockIdx.x * RU_ELEMS;
     const double *Vd = V + (int64_t)d * n + i0;
     double a[RU_EPL];
@@ -510,7 +489,7 @@ __global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate_next(int64_t n, int 
     for (int r = 0; r < RU_EPL; ++r) a[r] = 0.0;
     int k = sl;
     for (; k + RU_SLICES < nv; k += 2 * RU_SLICES) {
-        const double c0 = cf(k), c1 = cf(k + RU_SLICES);
+        const double c0 = coef[k * C + d], c1 = coef[(k + RU_SLICES) * C + d];
         const double *v0 = Vd + (int64_t)k * vstride, *v1 = v0 + (int64_t)RU_SLICES * vstride;
 #pragma unroll
         for (int r = 0; r < RU_EPL; ++r) {
@@ -519,7 +498,7 @@ __global__ void __launch_bounds__(32 * RU_SLICES) k_rupdate_next(int64_t n, int 
         }
     }
     if (k < nv) {
-        const double c0 = cf(k);
+        const double c0 = coef[k * C + d];
         const double *v0 = Vd + (int64_t)k * vstride;
 #pragma unroll
         for (int r = 0; r < RU_EPL; ++r) {
@@ -962,14 +941,6 @@ struct Arnoldi {
         return WFQ_OK;
     }
 
-    // partial dots of w with nv vectors V_0.. (stride vstride) into `partial` (nrb row blocks)
-    int dots_part(const double *V, int64_t vstride, int nv, const double *w) {
-        dim3 grid((unsigned)nrb, (unsigned)((nv + KV - 1) / KV), (unsigned)C);
-        k_rdot_part<<<grid, 256, 0, s>>>(n, C, nv, V, vstride, w, rpb, partial.ptr); note_launch();
-        WFQ_CUDA(cudaGetLastError());
-        return WFQ_OK;
-    }
-
     // dots of w with nv vectors V_0.. (stride vstride), finished into H column j / coef / hn
     int dots(const double *V, int64_t vstride, int nv, const double *w, int mode, int m, int j, double *H, double *hn) {
         dim3 grid((unsigned)nrb, (unsigned)((nv + KV - 1) / KV), (unsigned)C);
@@ -1162,29 +1133,25 @@ int solve_gmres_shifted(wfq_geom *g, const SolveArgs &a, cudaStream_t s) {
         double *dvj = DV.ptr + (int64_t)j * vstride;
         double *w = V.ptr + (int64_t)(j + 1) * vstride;
         WFQ_TRY(ar.dmul(dvj));
-        // w = (Kbar - P) D v_j, the first classical Gram-Schmidt pass's partial dots; the first
-        // update finishes them itself and forms the second pass's partial dots, the second
-        // update the norm's partial squares: 8 launches per step with the D product and the
-        // Givens step (12 with a launch per reduction)
+        // w = (Kbar - P) D v_j, the first classical Gram-Schmidt pass's dots; each update of
+        // the two passes forms the partial reductions of the next step (the second pass's
+        // dots, then the norm): 9 launches per step with the D product and the Givens step
+        // (12 with a launch per reduction).  Finishing the first pass's dots inside the first
+        // update as well (8 launches) measured slower: 102.3-102.7 against 101.1 ms per
+        // cnt20k step, the finish then a serial prologue of every update block.
         WFQ_TRY(ar.sparse(dvj, w));
         {
             KScope ko(ctx, WFQ_KT_ORTHO, s);
             const int nv = j + 1;
-            if (nv <= RU_FIN_MAX) {   // the first pass's dots finished inside the update
-                WFQ_TRY(ar.dots_part(V.ptr, vstride, nv, w));
-                k_rupdate_next<NEXT_DOTS><<<dim3((unsigned)ar.nbru, (unsigned)C), 32 * RU_SLICES, sizeof(double) * nv, s>>>(
-                    n, (int)C, nv, V.ptr, vstride, nullptr, w, ar.partial_f.ptr, ar.partial.ptr, ar.nrb, m, j, H.ptr);
-            } else {
-                WFQ_TRY(ar.dots(V.ptr, vstride, nv, w, RF_SET, m, j, H.ptr, hn.ptr));
-                k_rupdate_next<NEXT_DOTS><<<dim3((unsigned)ar.nbru, (unsigned)C), 32 * RU_SLICES, 0, s>>>(
-                    n, (int)C, nv, V.ptr, vstride, ar.coef.ptr, w, ar.partial_f.ptr, nullptr, 0, m, j, H.ptr);
-            }
+            WFQ_TRY(ar.dots(V.ptr, vstride, nv, w, RF_SET, m, j, H.ptr, hn.ptr));
+            k_rupdate_next<NEXT_DOTS><<<dim3((unsigned)ar.nbru, (unsigned)C), 32 * RU_SLICES, 0, s>>>(
+                n, (int)C, nv, V.ptr, vstride, ar.coef.ptr, w, ar.partial_f.ptr);
             note_launch();
             k_rdot_fin<<<nblk((int64_t)nv * C * 32), 256, 0, s>>>(ar.nbru, nv, (int)C, RF_ADD, ar.partial_f.ptr, m, j,
                                                                   H.ptr, ar.coef.ptr, hn.ptr);
             note_launch();
             k_rupdate_next<NEXT_NORM><<<dim3((unsigned)ar.nbru, (unsigned)C), 32 * RU_SLICES, 0, s>>>(
-                n, (int)C, nv, V.ptr, vstride, ar.coef.ptr, w, ar.partial_f.ptr, nullptr, 0, m, j, H.ptr);
+                n, (int)C, nv, V.ptr, vstride, ar.coef.ptr, w, ar.partial_f.ptr);
             note_launch();
             k_rscale_norm<<<nblk(n * C, 1024), 256, sizeof(double) * C, s>>>(n, (int)C, ar.nbru, ar.partial_f.ptr, m,
                                                                              j, H.ptr, hn.ptr, w, w, ar.xh.ptr,
