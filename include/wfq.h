@@ -327,9 +327,19 @@ int wfq_rhs(wfq_geom *g, int ndir, const double *dirs, double E0, double *R, voi
  *         complex64 basis (FP64-grade inner products, FP64 norms and Givens rotations);
  *         a cycle starts from the true residual at FP64 accuracy (iterative refinement)
  *         -- or, while every column is still above 1e-3 ||R||, from the mixed-operator
- *         residual; a column whose true residual shrank by less than 2x in each of two
- *         consecutive cycles is finished by plain FP64 GMRES(m) from its iterate.
- *         Convergence is always decided on the FP64-accuracy true residual.
+ *         residual.  A column is finished by plain FP64 GMRES(m) from its iterate when its
+ *         true residual shrank by less than 2x in each of two consecutive cycles while the
+ *         inner solve reached its own target (the mixed operator's residual estimate below
+ *         a quarter of the true residual: a precision floor), or in each of 20 consecutive
+ *         cycles otherwise.  The true residuals use double-float D products (stored float
+ *         pairs, else D regenerated per product); on a geometry with no stored D whose
+ *         regenerated residual reaches such a floor, the residuals switch to D regenerated
+ *         in FP64 and the column stays in mixed precision.
+ *         Convergence is always decided on the FP64-accuracy true residual (FP64 solves:
+ *         FP64 D products in the residual; their Arnoldi products on a geometry without
+ *         an FP64 D are the double-float ones).
+ * With the environment variable WFQ_TRACE set (not "0"), the solvers print one line per
+ * restart cycle (active and escalated columns, steps, worst true residual) on stderr.
  * q: output, N x ncols complex128 atom-major.  stats: host array of ncols, or NULL.
  * Returns WFQ_OK when every column converged, WFQ_ENOCONV otherwise (q holds the last
  * iterate), WFQ_ESINGULAR if some omega is 0.  Synchronises `stream`. */
@@ -364,10 +374,11 @@ int wfq_solve_gmres_shifted(wfq_geom *g, int64_t nfreq, const double *omega, int
  * which the operator apply already produces, so each iteration costs one D product.
  * With WFQ_PREC_MIXED the QMR recurrence restarts from the FP64 true residual every
  * `refine_every` iterations (0 = when its own residual estimate converges, at the latest
- * after 300 iterations); a column whose true residual shrank by less than 2x in two
- * consecutive restarts, or whose recurrence broke down, is finished by plain FP64
- * GMRES(50) from its iterate.  Returns WFQ_EBREAKDOWN if rho or sigma vanishes in some
- * column of an FP64 solve. */
+ * after 300 iterations); a column whose recurrence broke down, or whose true residual
+ * shrank by less than 2x in two consecutive restarts after each of which the inner QMR had
+ * converged (in 20 consecutive restarts otherwise), is finished by plain FP64 GMRES(50) from
+ * its iterate; the residual switch of a matrix-free geometry is as in wfq_solve_gmres.
+ * Returns WFQ_EBREAKDOWN if rho or sigma vanishes in some column of an FP64 solve. */
 int wfq_solve_qmr(wfq_geom *g, int64_t nfreq, const double *omega, int ndir,
                   const double *dirs, double E0, double rel_tol, int max_iter, int prec,
                   int refine_every, double *q, wfq_stats *stats, void *stream);
