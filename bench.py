@@ -245,6 +245,27 @@ def oracle_sample(wl, budget_s, cols):
     return solved, t_total, alphas, os.cpu_count()
 
 
+def audit_row_probabilities(R):
+    """Row-sampling probabilities of the residual audit: half uniform, half proportional
+    to |R_i|^2 (the residual of a Krylov iterate lives where R does -- at edges and
+    vacancies -- so sampling there cuts the estimate's variance; the uniform half keeps
+    every row reachable, so the estimate stays unbiased whatever the residual's shape)."""
+    a2 = np.abs(np.asarray(R)) ** 2
+    return 0.5 / len(a2) + 0.5 * a2 / a2.sum()
+
+
+def sampled_residual_estimate(r_rows, p_rows, r_full_norm, seed=20210308, nboot=2000):
+    """||r|| / ||R|| from the residual's rows r_s at rows drawn with replacement with
+    probabilities p_s: ||r||^2 ~ mean(|r_s|^2 / p_s) (unbiased), with a 95% bootstrap
+    interval (the draws resampled with replacement)."""
+    t = np.abs(np.asarray(r_rows)) ** 2 / np.asarray(p_rows)
+    est = float(np.sqrt(t.mean()) / r_full_norm)
+    rng = np.random.default_rng(seed)
+    boot = np.sqrt(t[rng.integers(0, len(t), size=(nboot, len(t)))].mean(axis=1)) / r_full_norm
+    lo, hi = np.percentile(boot, [2.5, 97.5])
+    return est, float(lo), float(hi)
+
+
 def is_bem(wl):
     return "surface" in wl
 
@@ -565,19 +586,23 @@ def run_ours(args, rank, world, dist):
         from oracle import oracle as orc
         qh = q.cpu().numpy()
         rng_a = np.random.default_rng(20210307)
-        audit_rows = np.sort(rng_a.choice(n, size=48, replace=False))
         audits = []
         for c in sorted({0, ncols - 1}):
             f, d = divmod(c, nd)
+            Rfull = g.rhs(dirs[d:d + 1])[:, 0]
+            # 48 rows drawn with replacement, half uniformly, half where R is large; the
+            # oracle recomputes each distinct row once
+            pr = audit_row_probabilities(Rfull)
+            draws = rng_a.choice(n, size=48, replace=True, p=pr)
+            audit_rows, inv = np.unique(draws, return_inverse=True)
             Rr = orc.rhs_rows(xyz, p, dirs[d], audit_rows)
             yr, _ = orc.apply_rows(xyz, p, orc.z_of_omega(om[f], p), qh[:, c], audit_rows)
-            Rfull = g.rhs(dirs[d:d + 1])[:, 0]
-            # ||r|| estimated from the sampled rows (N times their mean square) over the exact
-            # ||R|| (the library's R, which the oracle's R rows confirm); R itself is
-            # concentrated at edges and vacancies, so its own sampled mean would be biased
-            r_est = float(np.sqrt(n * np.mean(np.abs(Rr - yr) ** 2)) / np.linalg.norm(Rfull))
-            audits.append({"column": int(c), "sampled_rows": len(audit_rows),
+            # ||r|| estimated from the drawn rows over the exact ||R|| (the library's R,
+            # which the oracle's R rows confirm)
+            r_est, r_lo, r_hi = sampled_residual_estimate((Rr - yr)[inv], pr[draws], np.linalg.norm(Rfull))
+            audits.append({"column": int(c), "sampled_rows": len(audit_rows), "draws": len(draws),
                            "rel_residual_estimate_from_sampled_rows": r_est,
+                           "estimate_bootstrap_95": [r_lo, r_hi],
                            "R_rows_vs_library": float(np.abs(Rr - Rfull[audit_rows]).max() / np.abs(Rfull).max()),
                            "library_rel_residual": float(st_last[c]["rel_residual"])})
         out["accuracy"]["oracle_residual_audit"] = audits
