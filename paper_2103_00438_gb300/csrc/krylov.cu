@@ -1292,9 +1292,9 @@ static int qmr_impl(wfq_geom *g, const SolveArgs &a, cudaStream_t s, GmresOut *o
         }
         if (tighten) {
             // the floor is the residual's: recompute it with D in FP64 and carry on in mixed
-            // precision (columns whose QMR broke down still leave)
-            esc.erase(std::remove_if(esc.begin() + (std::ptrdiff_t)esc0, esc.end(), [&](int c) { return !brk_h[c]; }),
-                      esc.end());
+            // precision (the classification below this `continue` escalates the columns whose
+            // QMR broke down again, so none stays listed twice)
+            esc.resize(esc0);
             cm.residual_exact = true;
             std::fill(flat.begin(), flat.end(), 0);
             std::fill(slow_runs.begin(), slow_runs.end(), 0);
