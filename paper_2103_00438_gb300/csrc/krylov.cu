@@ -23,12 +23,12 @@
 
 namespace wfq {
 
-// FP64-grade product inside the solvers' FP64 iterations and residuals. With no FP64 D
-// stored, the double-float product (~2^-48 per product, on the FP32 pipes: float pairs
-// read from the stored planes or tiles for few columns, D regenerated per product
-// otherwise) instead of D regenerated in FP64: on GB300's FP64 rate the latter is ~8 s per
-// 192-column product at 1.5e5 atoms and ~100 s per 32-column product at 10^6 atoms, the
-// double-float forms 4 to 6 times less.
+// FP64-grade product of the FP64 solvers' Arnoldi and QMR iterations (their true residuals
+// take d_apply_fp64). With no FP64 D stored, the double-float product (~2^-48 per product,
+// on the FP32 pipes: the stored float-pair planes or tiles, else D regenerated per product)
+// instead of D regenerated in FP64: on GB300's FP64 rate the latter is ~8 s per 192-column
+// product at 1.5e5 atoms and ~100 s per 32-column product at 10^6 atoms, the double-float
+// forms 4 to 6 times less.
 static int solver_fp64_product(const wfq_geom *g, int64_t cc, const double2 *X, double2 *U, cudaStream_t s) {
     if (!g->D64 && g->op == OP_WFQ) return d_apply_df(g, cc, X, U, s);
     return d_apply_fp64(g, cc, X, U, s);
