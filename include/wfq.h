@@ -117,12 +117,15 @@ enum {
                               and after wfq_fmm_build, by the fast multipole method (as
                               WFQ_PREC_FMM, up to 256 columns per product); complex64
                               vectors; solves add iterative refinement on top, whose true
-                              residual uses WFQ_PREC_DF (FP64 kernels when D64 is not
-                              stored) */
-    WFQ_PREC_DF = 2,       /* wfq_apply only: complex128 vectors, D.x with FP64 operands split
-                              into float pairs and double-float accumulation (~2^-48 relative
-                              per product) on the FP32 pipes; needs WFQ_STORE_FP64 and more
-                              than 4 columns, else identical to WFQ_PREC_FP64 */
+                              residuals use the WFQ_PREC_DF product (on a geometry with no
+                              stored D, D regenerated in FP64 once that product's rounding
+                              holds a residual at a floor) */
+    WFQ_PREC_DF = 2,       /* wfq_apply and the refinement residuals: complex128 vectors, D.x
+                              with float-pair operands and double-float accumulation (~2^-48
+                              relative per product) on the FP32 pipes: D split from the stored
+                              FP64 D (up to 4 columns: the FP64 GEMV), or read from the stored
+                              FP32 pair planes or symmetric tiles, or regenerated from the
+                              coordinates in double-float (near pairs in FP64) */
     WFQ_PREC_FMM = 3       /* wfq_apply only: complex64 vectors, D.x by the fast multipole
                               method built with wfq_fmm_build (near field by Eq. 3, far field
                               1/r by Chebyshev interpolation), FP32 arithmetic */
